@@ -1,0 +1,417 @@
+"""Benchmark: reciprocal averaged-intensity evaluations per second on one GB300.
+
+One step = one cold reciprocal evaluation of the 200-lambda collimator workload
+(500 cells, nx = 4040, ny = 160, 646k unknowns, annular light 10-30 deg, output angle
+0): new pillar widths -> raster + assembly -> block-cyclic-reduction factorisation ->
+reciprocal solve with FP64 stencil refinement -> FP64 Toeplitz quadratic form (every
+row of the hot path except the brute-force comparison, which is timed separately on
+the same factorisation and reported under "bruteforce").
+
+Timed on the device with CUDA events on the library's stream, after W warm-up steps,
+bracketed by a barrier and synchronisation; the factor store (1.2 GB in FP32, 2.5 GB in
+FP64) is far larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp32|fp64]
+  python bench.py --impl reference ...   (the FP64 CPU oracle, time-boxed)
+
+Multi-GPU (torchrun): replicas only -- each rank evaluates its own designs; value is
+the total over ranks divided by the slowest rank's time ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "reciprocal avg-intensity evals/s at 200λ (FP32+refine vs FP64), p50/p99 ms"
+WORKLOAD = "c2_collimator"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _roofline(fam: str, stats: dict, prec: int, peaks: dict, peak_kind: str):
+    """Roofline record for one kernel family from the library's profiler totals."""
+    ms = stats["ms"]
+    if ms <= 0:
+        return None
+    if fam in ("gemm", "invert", "level0"):
+        tflops = stats["flops"] / (ms * 1e-3) / 1e12
+        if prec == 0:
+            peak, src = FP64_NOMINAL_TFLOPS, "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"
+        else:
+            peak = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            src = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"
+        return {"bound": "alu", "achieved": round(tflops, 3), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(tflops / peak, 4), "traffic": None,
+                "kernel": fam, "peak_source": src}
+    if fam == "qform":
+        tflops = stats["flops"] / (ms * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": round(tflops, 4), "peak": FP64_NOMINAL_TFLOPS,
+                "unit": "TFLOP/s", "frac": round(tflops / FP64_NOMINAL_TFLOPS, 4),
+                "traffic": None, "kernel": fam, "peak_source": "FP64 nominal"}
+    gbs = stats["bytes"] / (ms * 1e-3) / 1e9
+    peak = peaks.get("hbm_gbs", 6800.0)
+    return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(gbs / peak, 4), "traffic": None, "kernel": fam,
+            "peak_source": f"{peak_kind} HBM copy bandwidth"}
+
+
+def _cpu_baseline(timeout_s: float = 240.0):
+    """The oracle as it stands, one cold C2 evaluation, single-threaded, in a child."""
+    code = (
+        "import sys,time,json; sys.path.insert(0, %r)\n"
+        "import workloads as W\n"
+        "from oracle.reciprocal import timed_reciprocal\n"
+        "wl = W.c2_collimator(); ws = W.widths(500, 12345)\n"
+        "F, t = timed_reciprocal(wl, ws)\n"
+        "print(json.dumps({'F': F, 'seconds': t}))\n" % ROOT)
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+              "NUMEXPR_NUM_THREADS", "VECLIB_MAXIMUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                           timeout=timeout_s, env=env)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:  # noqa: BLE001
+        return {"value": None, "unit": "evals/s", "cores": 1, "kind": "oracle",
+                "sample": f"failed: {type(e).__name__}"}
+    return {"value": round(1.0 / d["seconds"], 5), "unit": "evals/s", "cores": 1,
+            "kind": "oracle", "seconds_per_eval": round(d["seconds"], 3),
+            "sample": "one cold evaluation of the full 200-lambda workload (raster, assembly, "
+                      "SuperLU factor, double-double refined solve, direct quadratic form), "
+                      "single thread"}
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on the same workload and metric (time-boxed)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    import workloads as W
+    from oracle.reciprocal import timed_reciprocal
+    wl = W.WORKLOADS[WORKLOAD]()
+    budget = float(os.environ.get("RCI_REFERENCE_BUDGET_S", "150"))
+    t_warm = None
+    for w in range(min(args.warmup, 1)):
+        _, t_warm = timed_reciprocal(wl, W.widths(wl.grid.n_cells, 900000 + w))
+    per = t_warm or 15.0
+    k_run = max(1, min(args.steps, int(budget // per)))
+    times = []
+    for k in range(k_run):
+        _, t = timed_reciprocal(wl, W.widths(wl.grid.n_cells, 1000 + k))
+        times.append(t)
+    total = sum(times)
+    value = k_run / total
+    ms = [t * 1e3 for t in times]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "evals/s",
+        "n_gpus": 1, "steps": args.steps, "steps_run": k_run, "warmup": args.warmup,
+        "ms_per_step": round(total / k_run * 1e3, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "p50_ms": round(statistics.median(ms), 2), "p99_ms": round(max(ms), 2),
+        "config": {"workload": WORKLOAD, "nx": 4040, "ny": 160, "unknowns": 646400,
+                   "light": "annulus 10-30 deg", "objective": "planewave mode, 0 deg"},
+        "cpu_baseline": {"value": round(value, 5), "unit": "evals/s", "cores": 1,
+                         "kind": "oracle",
+                         "sample": f"{k_run} of {args.steps} cold evaluations of the full workload "
+                                   f"(time-boxed to {budget:.0f} s), single thread"},
+        "e2e": {"value": round(value, 5), "unit": "evals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import workloads as W
+    import paper_2207_10701_gb300 as P
+    from paper_2207_10701_gb300 import build as B
+
+    ws_, rank, local = _dist()
+    B.build()
+    torch.cuda.set_device(local)
+    if ws_ > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    peaks, peak_kind = _peaks()
+    wl = W.WORKLOADS[WORKLOAD]()
+    prec = P.FP64 if args.prec == "fp64" else P.FP32_REFINE
+    stream = torch.cuda.Stream(device=local)
+    nc = wl.grid.n_cells
+    K, Wm = args.steps, args.warmup
+    seeds = [rank * 1_000_000 + s for s in range(K + Wm)]
+    widths_dev = torch.tensor(np.stack([W.widths(nc, s) for s in seeds]), dtype=torch.float64,
+                              device=f"cuda:{local}")
+    g = P.Grid(wl.grid, prec=prec, device=local, stream=stream)
+
+    def step(i):
+        g.set_design(widths_dev[i])
+        g.factor()
+        return g.avg_intensity(wl.objective, wl.light)
+
+    for i in range(Wm):
+        step(i)
+    torch.cuda.synchronize()
+    _barrier(ws_)
+    clocks = ClockSampler(local)
+    clocks.start()
+    g.profile(True)
+    l0 = P.kernel_launches()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    torch.cuda.synchronize()
+    _barrier(ws_)
+    ev[0].record(stream)
+    Fs = []
+    infos = []
+    for k in range(K):
+        F, info = step(Wm + k)
+        ev[k + 1].record(stream)
+        Fs.append(F)
+        infos.append(info)
+    torch.cuda.synchronize()
+    _barrier(ws_)
+    launches = P.kernel_launches() - l0
+    prof = g.profile_read()
+    g.profile(False)
+    clk = clocks.stop()
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(K)]
+    total_ms = ev[0].elapsed_time(ev[K])
+    total_ms = _max_over_ranks(total_ms, ws_)
+    value = ws_ * K / (total_ms * 1e-3)
+
+    # ---- end to end through the public API with host buffers (H2D widths, D2H result)
+    widths_host = [np.ascontiguousarray(W.widths(nc, 500_000 + rank * 1000 + k))
+                   for k in range(K)]
+    torch.cuda.synchronize()
+    _barrier(ws_)
+    t0 = time.perf_counter()
+    e2e_iters = 0
+    for k in range(K):
+        g.set_design(widths_host[k])
+        g.factor()
+        _, inf = g.avg_intensity(wl.objective, wl.light)
+        e2e_iters += inf.refine_iters
+    torch.cuda.synchronize()
+    e2e_s = _max_over_ranks(time.perf_counter() - t0, ws_)
+    e2e_value = ws_ * K / e2e_s
+    d2h = 8 + 4 + 8 * (e2e_iters / K + 1 + (1 if prec == P.FP64 else 0))
+
+    line = None
+    if rank == 0:
+        fams = {f: v for f, v in prof.items() if v["ms"] > 0}
+        dom = max(fams, key=lambda f: fams[f]["ms"])
+        roof = _roofline(dom, fams[dom], prec, peaks, peak_kind)
+        kernels = {}
+        for f, v in fams.items():
+            r = _roofline(f, v, prec, peaks, peak_kind)
+            kernels[f] = {"ms_per_step": round(v["ms"] / K, 4),
+                          "share": round(v["ms"] / sum(x["ms"] for x in fams.values()), 4),
+                          "launches_per_step": v["launches"] / K,
+                          "achieved": r["achieved"] if r else None,
+                          "unit": r["unit"] if r else None, "frac": r["frac"] if r else None}
+        ps = sorted(per)
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "evals/s", "n_gpus": ws_,
+            "steps": K, "warmup": Wm, "ms_per_step": round(total_ms / K, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64refine" if prec == P.FP32_REFINE else "f64",
+            "data": "synthetic",
+            "p50_ms": round(ps[len(ps) // 2], 4),
+            "p99_ms": round(ps[min(len(ps) - 1, int(math.ceil(0.99 * len(ps))) - 1)], 4),
+            "config": {"workload": WORKLOAD, "nx": g.nx, "ny": g.ny, "unknowns": g.N,
+                       "cells": nc, "light": "annulus 10-30 deg",
+                       "objective": "planewave mode, 0 deg",
+                       "precision": args.prec, "parallelism": f"replicas x{ws_}",
+                       "l2": "no flush: factor store %.2f GB > 129 MB L2"
+                             % (g.device_bytes() / 1e9),
+                       "refine_iters_mean": round(sum(i.refine_iters for i in infos) / K, 2),
+                       "rel_residual_max": max(i.rel_residual for i in infos)},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "kernels": kernels,
+            "clocks": clk,
+            "e2e": {"value": round(e2e_value, 3), "unit": "evals/s",
+                    "h2d_bytes_per_step": 8 * nc, "d2h_bytes_per_step": int(round(d2h))},
+            "F_last": Fs[-1],
+        }
+    g.close()
+
+    # ---- FP64 form and brute-force comparison (rank 0, outside the timed region)
+    if rank == 0 and not args.quick:
+        extra = {}
+        other = P.FP64 if prec == P.FP32_REFINE else P.FP32_REFINE
+        with P.Grid(wl.grid, prec=other, device=local, stream=stream) as g2:
+            t = []
+            for k in range(args.other_steps + 1):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g2.set_design(widths_dev[Wm + k % K])
+                g2.factor()
+                F2, _ = g2.avg_intensity(wl.objective, wl.light)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if k:
+                    t.append(e0.elapsed_time(e1))
+            t.sort()
+            extra["fp64" if other == P.FP64 else "fp32_refine"] = {
+                "evals_per_s": round(1e3 / (sum(t) / len(t)), 3), "p50_ms": round(t[len(t) // 2], 3),
+                "p99_ms": round(t[-1], 3), "steps": len(t)}
+        with P.Grid(wl.grid, prec=prec, device=local, stream=stream) as g3:
+            g3.set_design(widths_dev[Wm])
+            g3.factor()
+            Fr, _ = g3.avg_intensity(wl.objective, wl.light)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            Fb, _, binfo = g3.avg_bruteforce(wl.objective, wl.light, wl.n_angles)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tb = e0.elapsed_time(e1)
+            e0.record(stream)
+            Fr2, rinfo = g3.avg_intensity(wl.objective, wl.light)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tr = e0.elapsed_time(e1)
+            extra["bruteforce"] = {
+                "angles": wl.n_angles, "ms": round(tb, 2),
+                "reciprocal_warm_ms": round(tr, 3),
+                "time_ratio_brute_over_reciprocal": round(tb / tr, 1),
+                "F_reciprocal": Fr, "F_bruteforce": Fb,
+                "rel_diff": abs(Fb - Fr) / abs(Fr)}
+        line.update(extra)
+    if rank == 0 and not args.no_cpu_baseline and ws_ == 1:
+        line["cpu_baseline"] = _cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws_ > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--other-steps", type=int, default=5)
+    ap.add_argument("--quick", action="store_true", help="skip the FP64 / brute-force extras")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "ours":
+        args.warmup = max(3, args.warmup)   # never time fewer than 3 warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,240 @@
+/*
+ * rci.h -- C ABI of the GB300 reciprocal incoherent-light evaluator.
+ *
+ * The library computes the average figure of merit <|w^dag u|^2> of a 2-D
+ * metasurface under incoherent light with a single "reciprocal" frequency-domain
+ * solve v = A^{-dag} w followed by the quadratic form v^dag W v against the
+ * light's cross-correlation W (paper Sec. 4.1, Eq. 7), and, as the in-run
+ * comparison, the brute-force angle average of Eq. 6 as a multi-right-hand-side
+ * solve on the same factorisation (Sec. 5.2).
+ *
+ * Discretisation (the paper keeps the operator abstract, Sec. 4.1; this is the
+ * library's reading): scalar Helmholtz at wavelength 1 on a uniform grid
+ * h = 1/ppl, stretched-coordinate PML on all four sides, multiplied by s_x s_y so
+ * that A is complex symmetric (A = A^T).  Unknowns are ordered k = i*ny + j (x
+ * outermost), which makes A block tridiagonal along the metasurface with
+ * tridiagonal ny x ny diagonal blocks and diagonal couplings.
+ *   node (i, j): x_i = (i - npml + 1/2) h, y_j = (j + 1/2) h
+ *   nx = n_cells*cell_px + 2*npml; interior columns S = [npml, nx - npml), n_src = |S|
+ *   source row j_src = npml + src_offset; pillars in rows
+ *   [npml + rows_sub, npml + rows_sub + rows_pillar); substrate below, air above.
+ *
+ * Memory and ownership.  A grid owns all of its device memory (allocated at
+ * rci_create_grid / first use, released by rci_destroy_grid).  The caller owns
+ * every buffer it passes.  Each pointer argument states whether it is HOST or
+ * DEVICE memory.  Complex vectors are interleaved (re, im) float64 pairs.
+ *
+ * Streams.  All device work of a grid runs on the stream given at creation
+ * (NULL = legacy default stream).  Calls that return a host scalar synchronise
+ * that stream before returning.  A grid must not be used by two host threads
+ * at once.
+ *
+ * Errors.  Every call returns an rci_status.  Outputs are written only on
+ * RCI_OK, except RCI_ENOCONV, which still returns the best value reached (with
+ * the info record filled).  rci_last_error() gives a message for the last
+ * failure on a grid.  No exception crosses the ABI.
+ */
+#ifndef RCI_H
+#define RCI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RCI_OK = 0,
+  RCI_EINVAL = 1,     /* bad argument or size */
+  RCI_ENOMEM = 2,     /* device allocation failed */
+  RCI_ECUDA = 3,      /* a CUDA call failed */
+  RCI_ESTATE = 4,     /* call out of order (no design, not factored) */
+  RCI_ESINGULAR = 5,  /* zero pivot in a block inversion */
+  RCI_ENOCONV = 6,    /* iterative refinement did not reach the tolerance */
+  RCI_ENUMERIC = 7,   /* NaN or Inf in an input or result */
+  RCI_ETIMEOUT = 8    /* a bounded device wait expired */
+} rci_status;
+
+typedef enum {
+  RCI_FP64 = 0,        /* factor, solve and residual in FP64 */
+  RCI_FP32_REFINE = 1  /* factor and solve in FP32, FP64 stencil residual refinement */
+} rci_precision;
+
+typedef enum {
+  RCI_OBJ_POINT = 0,          /* concentrator, focus on node (i_f, j_f): w = e_f */
+  RCI_OBJ_PLANEWAVE = 1,      /* collimator: w_i = exp(i k0 sin(theta_out) x_i) on monitor_row, i in S */
+  RCI_OBJ_VIRTUAL_FOCUS = 2,  /* concentrator, focus d_rows above monitor_row at x_f:
+                                 w_i = conj(K(x_f - x_i)) on monitor_row, i in S, with K the
+                                 lattice propagator through homogeneous air (see rci_solve_reciprocal) */
+  RCI_OBJ_USER_ROW = 3        /* w given by the caller on monitor_row, i in S */
+} rci_objective_kind;
+
+typedef enum {
+  RCI_LIGHT_CONE = 0,      /* rho uniform in theta on [-c, c] */
+  RCI_LIGHT_ANNULUS = 1,   /* rho uniform in theta on [th1, th2] U [-th2, -th1] */
+  RCI_LIGHT_USER_LAGS = 2  /* real, even W given as lags W(m h), m = 0..n_src-1 */
+} rci_light_kind;
+
+/* Problem geometry (lengths in wavelengths, counts in grid cells). */
+typedef struct {
+  int32_t n_cells;      /* unit cells (one pillar each) */
+  int32_t ny;           /* rows, PML included */
+  int32_t ppl;          /* grid points per wavelength, h = 1/ppl */
+  int32_t cell_px;      /* unit-cell period in cells */
+  int32_t npml;         /* PML thickness in cells on all four sides */
+  int32_t rows_sub;     /* substrate rows between the bottom PML and the pillars */
+  int32_t rows_pillar;  /* pillar height in rows */
+  int32_t src_offset;   /* source row = npml + src_offset */
+  double eps_pillar, eps_sub, eps_air;
+  double pml_R0;        /* PML normal-incidence reflection target, sigma_max = -(m+1) ln(R0) / (2 d) */
+  int32_t pml_m;        /* PML polynomial grading order */
+  int32_t prec;         /* rci_precision */
+  int32_t device;       /* CUDA device ordinal */
+  int32_t reserved;
+} rci_grid_desc;
+
+typedef struct {
+  int32_t kind;          /* rci_objective_kind */
+  int32_t monitor_row;   /* PLANEWAVE / VIRTUAL_FOCUS / USER_ROW */
+  int32_t i_f, j_f;      /* POINT */
+  double theta_out;      /* PLANEWAVE: output angle in air (radians) */
+  double x_f;            /* VIRTUAL_FOCUS: focus abscissa (wavelengths) */
+  int32_t d_rows;        /* VIRTUAL_FOCUS: focus height above monitor_row (rows, >= 0) */
+  int32_t reserved;
+  const double* w_row;   /* USER_ROW: HOST complex128[n_src] (interleaved) */
+} rci_objective;
+
+typedef struct {
+  int32_t kind;          /* rci_light_kind */
+  int32_t reserved;
+  double c;              /* CONE half-angle (radians, 0 < c < pi/2) */
+  double th1, th2;       /* ANNULUS bounds (0 <= th1 < th2 < pi/2) */
+  const double* lags;    /* USER_LAGS: HOST float64[n_src] */
+} rci_light;
+
+typedef struct {
+  int32_t refine_iters;  /* refinement steps taken by the last solve */
+  int32_t reserved;
+  double rel_residual;   /* ||b - A x||_2 / ||b||_2 after the last solve (FP64 stencil) */
+  double ms_factor;      /* device time of the last factorisation */
+  double ms_solve;       /* device time of the last solve incl. refinement */
+  double ms_qform;       /* device time of the last quadratic form */
+} rci_info;
+
+typedef struct rci_grid rci_grid;
+
+/* Create a grid for one geometry on one device.  stream: cudaStream_t or NULL.
+ * Allocates the operator and factor storage for the descriptor's size.
+ * Errors: EINVAL (bad descriptor), ENOMEM, ECUDA. */
+rci_status rci_create_grid(const rci_grid_desc* desc, void* stream, rci_grid** out);
+
+/* Release every device allocation of the grid.  NULL is accepted. */
+rci_status rci_destroy_grid(rci_grid* g);
+
+/* Sizes and device footprint.  Any output pointer may be NULL. HOST outputs. */
+rci_status rci_grid_query(const rci_grid* g, int64_t* nx, int64_t* ny, int64_t* n_src,
+                          size_t* device_bytes);
+
+/* Set the pillar widths (wavelengths, one per cell, each in (0, period)) and
+ * assemble A: permittivity raster (area-weighted fill per column in the pillar
+ * rows) and the stretched-coordinate stencil.  Invalidates the factorisation.
+ * widths: HOST or DEVICE float64[n_cells] as widths_on_device says.  Host widths
+ * outside (0, period) fail here with EINVAL; device widths are checked on the device
+ * and the next rci_factor fails with EINVAL (the call itself does not synchronise). */
+rci_status rci_set_design(rci_grid* g, const double* widths, int64_t n_cells, int widths_on_device);
+
+/* Factor A by block cyclic reduction along x (the direct solver behind every
+ * solve; Sec. 4.1 asks for one solve per evaluation).  Precision per grid.
+ * Errors: ESTATE (no design), ESINGULAR (zero pivot in a diagonal block). */
+rci_status rci_factor(rci_grid* g);
+
+/* Solve A x = b for nrhs right-hand sides stored [i][j][q] (q fastest):
+ * b, x: DEVICE complex128[nx*ny*nrhs].  x may alias b.  FP32_REFINE grids refine
+ * every right-hand side with the FP64 stencil residual to rel. residual 1e-12;
+ * FP64 grids take up to two refinement steps.  info (HOST, may be NULL). */
+rci_status rci_solve(rci_grid* g, const double* b, double* x, int64_t nrhs, rci_info* info);
+
+/* Reciprocal solve of Eq. 7: v = A^{-dag} w = conj(A^{-1} conj(w)) (A symmetric).
+ * v_src_out: DEVICE complex128[n_src], v on the source row j_src over S, or NULL.
+ * v_full_out: DEVICE complex128[nx*ny], v on the whole grid, or NULL.
+ * For VIRTUAL_FOCUS the propagator is
+ *   K(D) = (h/pi) int_0^{pi/h} exp(i q(k) d_rows) cos(k D) dk,
+ *   cos q = 2 - cos(k h) - k0^2 h^2 eps_air / 2, q >= 0 or q = i alpha, alpha > 0,
+ * the exact continuation of a row of upward waves in homogeneous air on the
+ * infinite lattice, evaluated by composite Gauss-Legendre quadrature.
+ * Errors: ESTATE (not factored), EINVAL (objective outside the grid). */
+rci_status rci_solve_reciprocal(rci_grid* g, const rci_objective* obj, double* v_src_out,
+                                double* v_full_out, rci_info* info);
+
+/* Averaged figure of merit by reciprocity (Eq. 7): one reciprocal solve, then
+ *   F = sum_{i,l in S} conj(v_i) W(x_i - x_l) v_l
+ * with W(D) = int rho(theta) cos(theta) exp(i k_s sin(theta) D) dtheta, k_s = 2 pi sqrt(eps_sub)
+ * (closed forms: cone (sin c / c) sinc(k_s D sin c); annulus
+ * [sin th2 sinc(k_s D sin th2) - sin th1 sinc(k_s D sin th1)] / (th2 - th1)), in
+ * FP64 accumulation.  No h factors (arbitrary units).  out: HOST double. */
+rci_status rci_avg_intensity(rci_grid* g, const rci_objective* obj, const rci_light* light,
+                             double* out, rci_info* info);
+
+/* Brute-force average of Eq. 6 on the same factorisation: for each angle theta_q
+ * (measured in the substrate) the equivalent current b0 = sqrt(cos theta) exp(i k_s
+ * sin(theta) x_i) on row j_src over S, u_q = A^{-1} b0, f_q = |w^dag u_q|^2, and
+ *   avg = sum_q weight_q f_q.
+ * theta, weight: HOST float64[nq] (weight = quadrature weight times rho).
+ * fom_per_angle: HOST float64[nq] or NULL.  avg_out: HOST double or NULL. */
+rci_status rci_solve_angles(rci_grid* g, const rci_objective* obj, const double* theta,
+                            const double* weight, int64_t nq, double* fom_per_angle,
+                            double* avg_out, rci_info* info);
+
+/* Brute-force average with an nq-point Gauss-Legendre rule (Sec. 5.2) on the
+ * light's support (nq/2 points per interval for an annulus; nq even), rule built
+ * on the device.  Outputs as rci_solve_angles (HOST, may be NULL). */
+rci_status rci_avg_bruteforce(rci_grid* g, const rci_objective* obj, const rci_light* light,
+                              int64_t nq, double* fom_per_angle, double* avg_out, rci_info* info);
+
+/* FP64 Toeplitz quadratic form on the device:
+ *   out = sum_{i,l < n} conj(v_i) lags[|i - l|] v_l
+ * v: DEVICE complex128[n]; lags: DEVICE float64[n]; out: HOST double.
+ * stream: cudaStream_t or NULL.  Allocates and frees a small device scratch. */
+rci_status rci_qform_toeplitz(const double* v, const double* lags, int64_t n, double* out,
+                              void* stream);
+
+/* n-point Gauss-Legendre rule on [a, b] computed on the device (Newton on the
+ * three-term recurrence).  nodes, weights: DEVICE float64[n], ascending nodes. */
+rci_status rci_gauss_legendre(int64_t n, double a, double b, double* nodes, double* weights,
+                              void* stream);
+
+/* Copies of the assembled problem, for inspection.  DEVICE outputs:
+ * eps: float64[nx*ny] ([i][j]);  y = A x: complex128[nx*ny] (FP64 stencil). */
+rci_status rci_get_eps(rci_grid* g, double* eps_out);
+rci_status rci_apply_operator(rci_grid* g, const double* x, double* y);
+
+/* ---- instrumentation (no counterpart in the paper; measurement support) ----
+ * Kernel families timed by the profiler:
+ *   0 level-0 tridiagonal factor and first Schur blocks, 1 block inversions,
+ *   2 factorisation GEMMs, 3 forward/backward substitution, 4 FP64 stencil residual,
+ *   5 quadratic form, 6 raster/assembly/right-hand sides. */
+#define RCI_PROFILE_FAMILIES 8
+typedef struct {
+  double ms[RCI_PROFILE_FAMILIES];      /* device time (CUDA events on the grid's stream) */
+  double flops[RCI_PROFILE_FAMILIES];   /* algorithmic flops of the timed work */
+  double bytes[RCI_PROFILE_FAMILIES];   /* algorithmic bytes of the timed work */
+  int64_t launches[RCI_PROFILE_FAMILIES];
+} rci_profile;
+
+/* on != 0: reset the totals and start bracketing kernel families with CUDA events
+ * (adds about a microsecond per family per call); on == 0: stop. */
+rci_status rci_profile_enable(rci_grid* g, int on);
+/* Totals since the last enable.  out: HOST. */
+rci_status rci_profile_read(rci_grid* g, rci_profile* out);
+/* Kernels launched by this library in this process so far. */
+uint64_t rci_kernel_launches(void);
+
+/* Static strings; never NULL. */
+const char* rci_status_str(rci_status s);
+const char* rci_last_error(const rci_grid* g);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RCI_H */

@@ -1,0 +1,1016 @@
+// Block cyclic reduction factor and solve (see bcr.cuh for the algebra).
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "bcr.cuh"
+
+namespace {
+
+// ===================================================================== level 0
+// Pivoted LU of the tridiagonal diagonal block T_r of an eliminated row r = 2k+1
+// (Gaussian elimination with adjacent-row interchanges): multipliers dl, inverse
+// pivots dinv, first and second superdiagonals du, du2 of U, and swap flags piv.
+template <typename T>
+__global__ void tri_factor_kernel(const double2* __restrict__ dg, const double2* __restrict__ cy,
+                                  int nx, int ny, int m0, cplx<T>* __restrict__ tdl,
+                                  cplx<T>* __restrict__ tdinv, cplx<T>* __restrict__ tdu,
+                                  cplx<T>* __restrict__ tdu2, uint8_t* __restrict__ tpiv,
+                                  int32_t* status) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m0) return;
+  int64_t r = 2 * (int64_t)k + 1;
+  const double2* d = dg + r * ny;
+  const double2* o = cy + r * ny;  // o[j] couples j and j+1
+  int64_t base = (int64_t)k * ny;
+  cplx<T> cur_d = ccast<T>(d[0]);
+  cplx<T> cur_du = ny > 1 ? ccast<T>(o[0]) : czero<T>();
+  bool sing = false;
+  for (int j = 0; j < ny - 1; ++j) {
+    cplx<T> bs = ccast<T>(o[j]);
+    cplx<T> dnext = ccast<T>(d[j + 1]);
+    cplx<T> dunext = (j + 1 < ny - 1) ? ccast<T>(o[j + 1]) : czero<T>();
+    if (cabs1(cur_d) >= cabs1(bs)) {
+      if (cabs1(cur_d) == T(0)) sing = true;
+      cplx<T> m = bs * crecip(cur_d);
+      tdl[base + j] = m;
+      tdinv[base + j] = crecip(cur_d);
+      tdu[base + j] = cur_du;
+      tdu2[base + j] = czero<T>();
+      tpiv[base + j] = 0;
+      cur_d = dnext - m * cur_du;
+      cur_du = dunext;
+    } else {
+      cplx<T> m = cur_d * crecip(bs);
+      tdl[base + j] = m;
+      tdinv[base + j] = crecip(bs);
+      tdu[base + j] = dnext;
+      tdu2[base + j] = dunext;
+      tpiv[base + j] = 1;
+      cur_d = cur_du - m * dnext;
+      cur_du = -(m * dunext);
+    }
+  }
+  if (cabs1(cur_d) == T(0)) sing = true;
+  tdinv[base + ny - 1] = crecip(cur_d);
+  tdl[base + ny - 1] = czero<T>();
+  tdu[base + ny - 1] = czero<T>();
+  tdu2[base + ny - 1] = czero<T>();
+  tpiv[base + ny - 1] = 0;
+  if (sing) atomicCAS(status, DEV_OK, DEV_SINGULAR);
+}
+
+template <typename T>
+struct TriRow {
+  const cplx<T>* dl;
+  const cplx<T>* dinv;
+  const cplx<T>* du;
+  const cplx<T>* du2;
+  const uint8_t* piv;
+};
+
+// Forward sweep (row interchanges and unit lower factor) for the right-hand side
+// rhs(j), writing y_j through store(j, y).
+template <typename T, typename Rhs, typename Store>
+__device__ __forceinline__ void tri_forward(const TriRow<T>& f, int n, Rhs rhs, Store store) {
+  cplx<T> cur = rhs(0);
+  for (int j = 0; j < n - 1; ++j) {
+    cplx<T> nb = rhs(j + 1);
+    if (f.piv[j]) {
+      store(j, nb);
+      cur = cfms(f.dl[j], nb, cur);
+    } else {
+      store(j, cur);
+      cur = cfms(f.dl[j], cur, nb);
+    }
+  }
+  store(n - 1, cur);
+}
+
+// Backward substitution with U (diag, du, du2); load(j) returns y_j, emit(j, g_j).
+template <typename T, typename Load, typename Emit>
+__device__ __forceinline__ void tri_backward(const TriRow<T>& f, int n, Load load, Emit emit) {
+  cplx<T> g1 = czero<T>(), g2 = czero<T>();  // g_{j+1}, g_{j+2}
+  for (int j = n - 1; j >= 0; --j) {
+    cplx<T> y = load(j);
+    y = cfms(f.du[j], g1, y);
+    y = cfms(f.du2[j], g2, y);
+    cplx<T> g = y * f.dinv[j];
+    emit(j, g);
+    g2 = g1;
+    g1 = g;
+  }
+}
+
+// Dense Schur blocks of the first reduced system, one block per kept row e = 2k:
+//   D'_k = T_e - diag(cx[e-1]) T_{e-1}^{-1} diag(cx[e-1]) - diag(cx[e]) T_{e+1}^{-1} diag(cx[e])
+//   L'_k = -diag(cx[e-1]) T_{e-1}^{-1} diag(cx[e-2])
+// Thread b forms column b of T^{-1} by a tridiagonal solve with the unit vector e_b,
+// using the output column as its temporary.
+template <typename T>
+__global__ void level0_schur_kernel(const double2* __restrict__ dg, const double2* __restrict__ cx,
+                                    const double2* __restrict__ cy, int nx, int ny, int m0,
+                                    const cplx<T>* __restrict__ tdl, const cplx<T>* __restrict__ tdinv,
+                                    const cplx<T>* __restrict__ tdu, const cplx<T>* __restrict__ tdu2,
+                                    const uint8_t* __restrict__ tpiv, cplx<T>* __restrict__ Dn,
+                                    cplx<T>* __restrict__ Ln) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cplx<T>* sm = reinterpret_cast<cplx<T>*>(sm_raw);
+  // [0,4ny): right factors, [4ny,8ny): left factors, then cxl2, cxl, cxr, dge, cye; piv bytes last
+  cplx<T>* R = sm;
+  cplx<T>* Lf = sm + 4 * ny;
+  cplx<T>* cxl2 = sm + 8 * ny;
+  cplx<T>* cxl = cxl2 + ny;
+  cplx<T>* cxr = cxl + ny;
+  cplx<T>* dge = cxr + ny;
+  cplx<T>* cye = dge + ny;
+  uint8_t* pivR = reinterpret_cast<uint8_t*>(cye + ny);
+  uint8_t* pivL = pivR + ny;
+
+  const int k = blockIdx.x;
+  const int64_t e = 2 * (int64_t)k;
+  const bool has_r = e + 1 < nx;   // eliminated row e+1 has index k
+  const bool has_l = e >= 1;       // eliminated row e-1 has index k-1
+  for (int j = threadIdx.x; j < ny; j += blockDim.x) {
+    if (has_r) {
+      int64_t b = (int64_t)k * ny + j;
+      R[j] = tdl[b];
+      R[ny + j] = tdinv[b];
+      R[2 * ny + j] = tdu[b];
+      R[3 * ny + j] = tdu2[b];
+      pivR[j] = tpiv[b];
+      cxr[j] = ccast<T>(cx[e * ny + j]);
+    }
+    if (has_l) {
+      int64_t b = (int64_t)(k - 1) * ny + j;
+      Lf[j] = tdl[b];
+      Lf[ny + j] = tdinv[b];
+      Lf[2 * ny + j] = tdu[b];
+      Lf[3 * ny + j] = tdu2[b];
+      pivL[j] = tpiv[b];
+      cxl[j] = ccast<T>(cx[(e - 1) * ny + j]);
+      cxl2[j] = ccast<T>(cx[(e - 2) * ny + j]);
+    }
+    dge[j] = ccast<T>(dg[e * ny + j]);
+    cye[j] = ccast<T>(cy[e * ny + j]);
+  }
+  __syncthreads();
+  const int b = threadIdx.x;
+  if (b >= ny) return;
+  cplx<T>* Dcol = Dn + (int64_t)k * ny * ny + b;
+  cplx<T>* Lcol = Ln + (int64_t)k * ny * ny + b;
+  auto Te = [&](int a) -> cplx<T> {
+    if (a == b) return dge[a];
+    if (a == b - 1) return cye[a];
+    if (a == b + 1) return cye[b];
+    return czero<T>();
+  };
+  auto unit = [&](int a) -> cplx<T> { return a == b ? mkc(T(1), T(0)) : czero<T>(); };
+  if (has_r) {
+    TriRow<T> f{R, R + ny, R + 2 * ny, R + 3 * ny, pivR};
+    tri_forward<T>(f, ny, unit, [&](int a, cplx<T> y) { Dcol[(int64_t)a * ny] = y; });
+    const cplx<T> sb = cxr[b];
+    tri_backward<T>(f, ny, [&](int a) { return Dcol[(int64_t)a * ny]; },
+                    [&](int a, cplx<T> g) { Dcol[(int64_t)a * ny] = cfms(cxr[a] * g, sb, Te(a)); });
+  } else {
+    for (int a = 0; a < ny; ++a) Dcol[(int64_t)a * ny] = Te(a);
+  }
+  if (has_l) {
+    TriRow<T> f{Lf, Lf + ny, Lf + 2 * ny, Lf + 3 * ny, pivL};
+    tri_forward<T>(f, ny, unit, [&](int a, cplx<T> y) { Lcol[(int64_t)a * ny] = y; });
+    const cplx<T> sl = cxl[b], sl2 = cxl2[b];
+    tri_backward<T>(f, ny, [&](int a) { return Lcol[(int64_t)a * ny]; },
+                    [&](int a, cplx<T> g) {
+                      cplx<T> cg = cxl[a] * g;
+                      Lcol[(int64_t)a * ny] = -(cg * sl2);
+                      Dcol[(int64_t)a * ny] = cfms(cg, sl, Dcol[(int64_t)a * ny]);
+                    });
+  }
+}
+
+// ===================================================================== Gauss-Jordan
+// In-place inversion with partial pivoting (largest |re|+|im| in the column, ties to
+// the lowest row).  Row interchanges are undone as column interchanges on output.
+// One block per matrix; the matrix lives in shared memory (SMEM) or in global memory
+// (the source slot, which is destroyed).
+constexpr int GJ_THREADS = 512;
+
+template <typename T, bool SMEM>
+__global__ void __launch_bounds__(GJ_THREADS)
+gj_inverse_kernel(cplx<T>* __restrict__ src, int64_t src_stride, cplx<T>* __restrict__ out,
+                  int64_t out_stride, int n, int32_t* status) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cplx<T>* rowk = reinterpret_cast<cplx<T>*>(sm_raw);
+  cplx<T>* colk = rowk + n;
+  int* perm = reinterpret_cast<int*>(colk + n);
+  int* idx = perm + n;
+  cplx<T>* a_s = reinterpret_cast<cplx<T>*>(sm_raw + (((size_t)2 * n * sizeof(cplx<T>) +
+                                                         (size_t)2 * n * sizeof(int) + 15) &
+                                                        ~(size_t)15));
+  __shared__ int s_p;
+  __shared__ cplx<T> s_pinv, s_pv, s_akk;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = GJ_THREADS / 32;
+  cplx<T>* g = src + (int64_t)blockIdx.x * src_stride;
+  cplx<T>* a = SMEM ? a_s : g;
+  if (SMEM) {
+    for (int e = tid; e < n * n; e += GJ_THREADS) a[e] = g[e];
+    __syncthreads();
+  }
+  bool sing = false;
+  for (int k = 0; k < n; ++k) {
+    if (warp == 0) {
+      T best = T(-1);
+      int bi = k;
+      for (int i = k + lane; i < n; i += 32) {
+        T v = cabs1(a[(int64_t)i * n + k]);
+        if (v > best) {
+          best = v;
+          bi = i;
+        }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        T ob = __shfl_down_sync(0xffffffffu, best, off);
+        int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        s_p = bi;
+        cplx<T> pv = a[(int64_t)bi * n + k];
+        s_pv = pv;
+        s_akk = a[(int64_t)k * n + k];
+        if (!(best > T(0))) sing = true;
+        s_pinv = crecip(pv);
+        perm[k] = bi;
+      }
+    }
+    __syncthreads();
+    const int p = s_p;
+    const cplx<T> pinv = s_pinv;
+    for (int t = tid; t < n; t += GJ_THREADS) {
+      colk[t] = (t == k) ? s_pv : (t == p ? s_akk : a[(int64_t)t * n + k]);
+      cplx<T> rk = a[(int64_t)k * n + t];
+      cplx<T> rp = a[(int64_t)p * n + t];
+      cplx<T> v = (t == k ? mkc(T(1), T(0)) : rp) * pinv;
+      if (p != k) a[(int64_t)p * n + t] = rk;
+      a[(int64_t)k * n + t] = v;
+      rowk[t] = v;
+    }
+    __syncthreads();
+    for (int i = warp; i < n; i += nwarps) {
+      if (i == k) continue;
+      const cplx<T> ci = colk[i];
+      cplx<T>* ar = a + (int64_t)i * n;
+      for (int j = lane; j < n; j += 32) {
+        cplx<T> base = (j == k) ? czero<T>() : ar[j];
+        ar[j] = cfms(ci, rowk[j], base);
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    for (int j = 0; j < n; ++j) idx[j] = j;
+    for (int k = n - 1; k >= 0; --k) {
+      int p = perm[k];
+      int t = idx[k];
+      idx[k] = idx[p];
+      idx[p] = t;
+    }
+    if (sing) atomicCAS(status, DEV_OK, DEV_SINGULAR);
+  }
+  __syncthreads();
+  cplx<T>* o = out + (int64_t)blockIdx.x * out_stride;
+  for (int e = tid; e < n * n; e += GJ_THREADS) {
+    int i = e / n, j = e - (e / n) * n;
+    o[e] = a[(int64_t)i * n + idx[j]];
+  }
+}
+
+template <typename T>
+size_t gj_smem_bytes(int n, bool smem_matrix) {
+  size_t head = (((size_t)2 * n * sizeof(cplx<T>) + (size_t)2 * n * sizeof(int) + 15) & ~(size_t)15);
+  return head + (smem_matrix ? (size_t)n * n * sizeof(cplx<T>) : 0);
+}
+
+constexpr size_t SMEM_LIMIT = 227 * 1024;
+
+template <typename T>
+cudaError_t launch_gj(cplx<T>* src, int64_t src_stride, cplx<T>* out, int64_t out_stride, int n,
+                      int batch, int32_t* status, cudaStream_t s) {
+  if (batch <= 0) return cudaSuccess;
+  size_t full = gj_smem_bytes<T>(n, true);
+  if (full <= SMEM_LIMIT) {
+    RCI_CUDA_TRY(cudaFuncSetAttribute(gj_inverse_kernel<T, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)full));
+    gj_inverse_kernel<T, true><<<batch, GJ_THREADS, full, s>>>(src, src_stride, out, out_stride, n,
+                                                               status); rci_note_launch();
+  } else {
+    size_t head = gj_smem_bytes<T>(n, false);
+    gj_inverse_kernel<T, false><<<batch, GJ_THREADS, head, s>>>(src, src_stride, out, out_stride,
+                                                                n, status); rci_note_launch();
+  }
+  return cudaGetLastError();
+}
+
+// ===================================================================== batched GEMM
+// C[z] = alpha op(A[z]) op(B[z]) + beta C0[z]   (row-major, complex, op = N or T,
+// no conjugation), z = blockIdx.z.  16 x 16 threads, each TM x TN outputs (strided
+// by 16 so shared-memory reads are conflict-free), K tiles of 16.
+template <typename T>
+struct GemmArgs {
+  int M, N, K;
+  const cplx<T>* A;
+  int64_t lda, sA;
+  const cplx<T>* B;
+  int64_t ldb, sB;
+  cplx<T>* C;
+  int64_t ldc, sC;
+  const cplx<T>* C0;
+  int64_t ldc0, sC0;
+  cplx<T> alpha, beta;
+};
+
+template <typename T, int TM, int TN, bool TA, bool TB>
+__global__ void __launch_bounds__(256) cgemm_kernel(GemmArgs<T> p) {
+  constexpr int BM = 16 * TM, BN = 16 * TN, BK = 16;
+  __shared__ cplx<T> As[BK][BM];
+  __shared__ cplx<T> Bs[BK][BN];
+  const int64_t z = blockIdx.z;
+  const cplx<T>* A = p.A + z * p.sA;
+  const cplx<T>* B = p.B + z * p.sB;
+  const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  cplx<T> acc[TM][TN];
+#pragma unroll
+  for (int r = 0; r < TM; ++r)
+#pragma unroll
+    for (int c = 0; c < TN; ++c) acc[r][c] = czero<T>();
+  for (int k0 = 0; k0 < p.K; k0 += BK) {
+#pragma unroll
+    for (int e = tid; e < BM * BK; e += 256) {
+      int i, kk;
+      if (!TA) {
+        i = e / BK;
+        kk = e - i * BK;
+      } else {
+        kk = e / BM;
+        i = e - kk * BM;
+      }
+      int gi = i0 + i, gk = k0 + kk;
+      cplx<T> v = czero<T>();
+      if (gi < p.M && gk < p.K) v = TA ? A[(int64_t)gk * p.lda + gi] : A[(int64_t)gi * p.lda + gk];
+      As[kk][i] = v;
+    }
+#pragma unroll
+    for (int e = tid; e < BK * BN; e += 256) {
+      int j, kk;
+      if (!TB) {
+        kk = e / BN;
+        j = e - kk * BN;
+      } else {
+        j = e / BK;
+        kk = e - j * BK;
+      }
+      int gj = j0 + j, gk = k0 + kk;
+      cplx<T> v = czero<T>();
+      if (gj < p.N && gk < p.K) v = TB ? B[(int64_t)gj * p.ldb + gk] : B[(int64_t)gk * p.ldb + gj];
+      Bs[kk][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      cplx<T> av[TM], bv[TN];
+#pragma unroll
+      for (int r = 0; r < TM; ++r) av[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < TN; ++c) bv[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < TM; ++r)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) acc[r][c] = cfma(av[r], bv[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+  cplx<T>* C = p.C + z * p.sC;
+  const cplx<T>* C0 = p.C0 ? p.C0 + z * p.sC0 : nullptr;
+#pragma unroll
+  for (int r = 0; r < TM; ++r) {
+    int gi = i0 + ty + 16 * r;
+    if (gi >= p.M) continue;
+#pragma unroll
+    for (int c = 0; c < TN; ++c) {
+      int gj = j0 + tx + 16 * c;
+      if (gj >= p.N) continue;
+      cplx<T> v = p.alpha * acc[r][c];
+      if (C0) v = cfma(p.beta, C0[(int64_t)gi * p.ldc0 + gj], v);
+      C[(int64_t)gi * p.ldc + gj] = v;
+    }
+  }
+}
+
+inline int pick_tile(int d) {
+  if (d % 80 == 0) return 5;
+  if (d % 64 == 0) return 4;
+  if (d % 48 == 0) return 3;
+  if (d <= 48) return 3;
+  return 4;
+}
+
+template <typename T, int TM, int TN>
+cudaError_t gemm_tn(const GemmArgs<T>& a, bool ta, bool tb, int batch, cudaStream_t s) {
+  dim3 grd((unsigned)ceil_div(a.N, 16 * TN), (unsigned)ceil_div(a.M, 16 * TM), (unsigned)batch);
+  if (!ta && !tb) cgemm_kernel<T, TM, TN, false, false><<<grd, 256, 0, s>>>(a);
+  else if (!ta && tb) cgemm_kernel<T, TM, TN, false, true><<<grd, 256, 0, s>>>(a);
+  else if (ta && !tb) cgemm_kernel<T, TM, TN, true, false><<<grd, 256, 0, s>>>(a);
+  else return cudaErrorInvalidValue;
+  rci_note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T, int TM>
+cudaError_t gemm_m(const GemmArgs<T>& a, bool ta, bool tb, int batch, cudaStream_t s) {
+  switch (pick_tile(a.N)) {
+    case 3: return gemm_tn<T, TM, 3>(a, ta, tb, batch, s);
+    case 5: return gemm_tn<T, TM, 5>(a, ta, tb, batch, s);
+    default: return gemm_tn<T, TM, 4>(a, ta, tb, batch, s);
+  }
+}
+
+// Batched GEMM with element strides between the batch members.
+template <typename T>
+cudaError_t gemm(int M, int N, int K, bool ta, bool tb, cplx<T> alpha, const cplx<T>* A,
+                 int64_t lda, int64_t sA, const cplx<T>* B, int64_t ldb, int64_t sB, cplx<T> beta,
+                 const cplx<T>* C0, int64_t ldc0, int64_t sC0, cplx<T>* C, int64_t ldc,
+                 int64_t sC, int batch, cudaStream_t s, Profiler* prof = nullptr,
+                 int fam = PF_GEMM) {
+  if (batch <= 0) return cudaSuccess;
+  if (batch > 65535) return cudaErrorInvalidValue;
+  ProfScope ps(prof, fam, s, 8.0 * M * N * K * (double)batch,
+               (double)sizeof(cplx<T>) * batch * ((double)M * K + (double)K * N + (double)M * N), 1);
+  GemmArgs<T> a{M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, C0, ldc0, sC0, alpha, beta};
+  switch (pick_tile(M)) {
+    case 3: return gemm_m<T, 3>(a, ta, tb, batch, s);
+    case 5: return gemm_m<T, 5>(a, ta, tb, batch, s);
+    default: return gemm_m<T, 4>(a, ta, tb, batch, s);
+  }
+}
+
+// ===================================================================== solve kernels
+// Level 0 forward: t0[k] = T_{2k+1}^{-1} b[2k+1] (one thread per (k, q)).
+template <typename T>
+__global__ void fwd0_kernel(const cplx<T>* __restrict__ b, cplx<T>* __restrict__ t0, int ny,
+                            int m0, int nrhs, const cplx<T>* tdl, const cplx<T>* tdinv,
+                            const cplx<T>* tdu, const cplx<T>* tdu2, const uint8_t* tpiv) {
+  int64_t tt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tt >= (int64_t)m0 * nrhs) return;
+  int k = (int)(tt / nrhs), q = (int)(tt - (int64_t)k * nrhs);
+  int64_t fb = (int64_t)k * ny;
+  TriRow<T> f{tdl + fb, tdinv + fb, tdu + fb, tdu2 + fb, tpiv + fb};
+  const cplx<T>* br = b + (2 * (int64_t)k + 1) * ny * nrhs + q;
+  cplx<T>* tr = t0 + (int64_t)k * ny * nrhs + q;
+  tri_forward<T>(f, ny, [&](int j) { return br[(int64_t)j * nrhs]; },
+                 [&](int j, cplx<T> y) { tr[(int64_t)j * nrhs] = y; });
+  tri_backward<T>(f, ny, [&](int j) { return tr[(int64_t)j * nrhs]; },
+                  [&](int j, cplx<T> g) { tr[(int64_t)j * nrhs] = g; });
+}
+
+// Level 0 kept rows: B1[k] = b[2k] - cx[2k-1] o t0[k-1] - cx[2k] o t0[k].
+template <typename T>
+__global__ void keep0_kernel(const cplx<T>* __restrict__ b, const cplx<T>* __restrict__ t0,
+                             const double2* __restrict__ cx, cplx<T>* __restrict__ B1, int nx,
+                             int ny, int n1, int nrhs) {
+  int64_t row = (int64_t)ny * nrhs;
+  int64_t tt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tt >= (int64_t)n1 * row) return;
+  int64_t k = tt / row, r = tt - k * row;
+  int j = (int)(r / nrhs);
+  cplx<T> v = b[2 * k * row + r];
+  if (k >= 1) v = cfms(ccast<T>(cx[(2 * k - 1) * ny + j]), t0[(k - 1) * row + r], v);
+  if (2 * k + 1 < nx) v = cfms(ccast<T>(cx[(2 * k) * ny + j]), t0[k * row + r], v);
+  B1[tt] = v;
+}
+
+// Level 0 back substitution: x[2k] = x1[k];
+// x[2k+1] = T^{-1}(b[2k+1] - cx[2k] o x1[k] - cx[2k+1] o x1[k+1]).
+template <typename T>
+__global__ void bwd0_kernel(const cplx<T>* b, const cplx<T>* __restrict__ x1,
+                            const double2* __restrict__ cx, cplx<T>* x, int nx, int ny, int n1,
+                            int nrhs, const cplx<T>* tdl, const cplx<T>* tdinv, const cplx<T>* tdu,
+                            const cplx<T>* tdu2, const uint8_t* tpiv) {
+  int64_t tt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tt >= (int64_t)n1 * nrhs) return;
+  int k = (int)(tt / nrhs), q = (int)(tt - (int64_t)k * nrhs);
+  int64_t row = (int64_t)ny * nrhs;
+  const cplx<T>* xa = x1 + (int64_t)k * row + q;
+  cplx<T>* xe = x + 2 * (int64_t)k * row + q;
+  for (int j = 0; j < ny; ++j) xe[(int64_t)j * nrhs] = xa[(int64_t)j * nrhs];
+  int64_t r = 2 * (int64_t)k + 1;
+  if (r >= nx) return;
+  const bool has_b = r + 1 < nx;
+  const cplx<T>* xb = x1 + (int64_t)(k + 1) * row + q;
+  const cplx<T>* br = b + r * row + q;
+  cplx<T>* xr = x + r * row + q;
+  const double2* cl = cx + (r - 1) * ny;
+  const double2* cr = cx + r * ny;
+  int64_t fb = (int64_t)k * ny;
+  TriRow<T> f{tdl + fb, tdinv + fb, tdu + fb, tdu2 + fb, tpiv + fb};
+  auto rhs = [&](int j) {
+    cplx<T> v = cfms(ccast<T>(cl[j]), xa[(int64_t)j * nrhs], br[(int64_t)j * nrhs]);
+    if (has_b) v = cfms(ccast<T>(cr[j]), xb[(int64_t)j * nrhs], v);
+    return v;
+  };
+  tri_forward<T>(f, ny, rhs, [&](int j, cplx<T> y) { xr[(int64_t)j * nrhs] = y; });
+  tri_backward<T>(f, ny, [&](int j) { return xr[(int64_t)j * nrhs]; },
+                  [&](int j, cplx<T> g) { xr[(int64_t)j * nrhs] = g; });
+}
+
+// Kept rows of a dense level: Bn[k] = B[2k] - Q[k-1] - P[k].
+template <typename T>
+__global__ void keep_kernel(const cplx<T>* __restrict__ B, const cplx<T>* __restrict__ P,
+                            const cplx<T>* __restrict__ Q, cplx<T>* __restrict__ Bn, int m, int nk,
+                            int64_t row) {
+  int64_t tt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tt >= (int64_t)nk * row) return;
+  int64_t k = tt / row, r = tt - k * row;
+  cplx<T> v = B[2 * k * row + r];
+  if (k >= 1) v = v - Q[(k - 1) * row + r];
+  if (k < m) v = v - P[k * row + r];
+  Bn[tt] = v;
+}
+
+// x_l[2k] = x_up[k] for every kept row.
+template <typename T>
+__global__ void copy_kept_kernel(const cplx<T>* __restrict__ xup, cplx<T>* __restrict__ xl, int nk,
+                                 int64_t row) {
+  int64_t tt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tt >= (int64_t)nk * row) return;
+  int64_t k = tt / row, r = tt - k * row;
+  xl[2 * k * row + r] = xup[tt];
+}
+
+// ----- single right-hand side: matrix-vector kernels, one block per eliminated row
+constexpr int GV_THREADS = 256, GV_WARPS = GV_THREADS / 32;
+
+template <typename T>
+__device__ __forceinline__ cplx<T> warp_sum(cplx<T> v) {
+  for (int off = 16; off > 0; off >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, off);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
+  }
+  return v;
+}
+
+// y = M x (M row-major ny x ny, x in shared memory); optional y = y0 - M x - M2 x2.
+template <typename T>
+__device__ void gemv_n(const cplx<T>* __restrict__ M, const cplx<T>* x, cplx<T>* y, int ny) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int a = warp; a < ny; a += GV_WARPS) {
+    cplx<T> acc = czero<T>();
+    const cplx<T>* Mr = M + (int64_t)a * ny;
+    for (int c = lane; c < ny; c += 32) acc = cfma(Mr[c], x[c], acc);
+    acc = warp_sum<T>(acc);
+    if (lane == 0) y[a] = acc;
+  }
+}
+
+// y = M^T x, columns spread over lanes, rows over warps, reduced through shared memory
+template <typename T, int CMAX>
+__device__ void gemv_t(const cplx<T>* __restrict__ M, const cplx<T>* x, cplx<T>* red, cplx<T>* y,
+                       int ny) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  cplx<T> acc[CMAX];
+#pragma unroll
+  for (int s = 0; s < CMAX; ++s) acc[s] = czero<T>();
+  for (int a = warp; a < ny; a += GV_WARPS) {
+    const cplx<T> xa = x[a];
+    const cplx<T>* Mr = M + (int64_t)a * ny;
+#pragma unroll
+    for (int s = 0; s < CMAX; ++s) {
+      int c = lane + 32 * s;
+      if (c < ny) acc[s] = cfma(Mr[c], xa, acc[s]);
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < CMAX; ++s) {
+    int c = lane + 32 * s;
+    if (c < ny) red[warp * ny + c] = acc[s];
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < ny; c += GV_THREADS) {
+    cplx<T> v = czero<T>();
+    for (int w = 0; w < GV_WARPS; ++w) v = v + red[w * ny + c];
+    y[c] = v;
+  }
+  __syncthreads();
+}
+
+template <typename T, int CMAX>
+__global__ void __launch_bounds__(GV_THREADS)
+fwd_gemv_kernel(const cplx<T>* __restrict__ Dinv, const cplx<T>* __restrict__ X,
+                const cplx<T>* __restrict__ Y, const cplx<T>* __restrict__ B,
+                cplx<T>* __restrict__ t, cplx<T>* __restrict__ P, cplx<T>* __restrict__ Q, int n,
+                int ny) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cplx<T>* bs = reinterpret_cast<cplx<T>*>(sm_raw);
+  cplx<T>* red = bs + ny;
+  const int64_t k = blockIdx.x;
+  const int64_t nn = (int64_t)ny * ny;
+  for (int c = threadIdx.x; c < ny; c += GV_THREADS) bs[c] = B[(2 * k + 1) * ny + c];
+  __syncthreads();
+  gemv_n<T>(Dinv + k * nn, bs, t + k * ny, ny);
+  gemv_t<T, CMAX>(X + k * nn, bs, red, P + k * ny, ny);
+  if (2 * k + 2 < n) gemv_t<T, CMAX>(Y + k * nn, bs, red, Q + k * ny, ny);
+}
+
+// x_l[2k] = x_up[k];  x_l[2k+1] = t[k] - X_k x_up[k] - Y_k x_up[k+1]
+template <typename T>
+__global__ void __launch_bounds__(GV_THREADS)
+bwd_gemv_kernel(const cplx<T>* __restrict__ X, const cplx<T>* __restrict__ Y,
+                const cplx<T>* __restrict__ t, const cplx<T>* __restrict__ xup,
+                cplx<T>* __restrict__ xl, int n, int m, int ny) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cplx<T>* xa = reinterpret_cast<cplx<T>*>(sm_raw);
+  cplx<T>* xb = xa + ny;
+  const int64_t k = blockIdx.x;
+  const int64_t nn = (int64_t)ny * ny;
+  const bool has_b = 2 * k + 2 < n;
+  for (int c = threadIdx.x; c < ny; c += GV_THREADS) {
+    cplx<T> v = xup[k * ny + c];
+    xa[c] = v;
+    xl[2 * k * ny + c] = v;
+    xb[c] = has_b ? xup[(k + 1) * ny + c] : czero<T>();
+  }
+  __syncthreads();
+  if (k >= m) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const cplx<T>* Xk = X + k * nn;
+  const cplx<T>* Yk = Y + k * nn;
+  for (int a = warp; a < ny; a += GV_WARPS) {
+    cplx<T> acc = czero<T>();
+    for (int c = lane; c < ny; c += 32) {
+      acc = cfma(Xk[(int64_t)a * ny + c], xa[c], acc);
+      if (has_b) acc = cfma(Yk[(int64_t)a * ny + c], xb[c], acc);
+    }
+    acc = warp_sum<T>(acc);
+    if (lane == 0) xl[(2 * k + 1) * ny + a] = t[k * ny + a] - acc;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(GV_THREADS)
+final_gemv_kernel(const cplx<T>* __restrict__ Dinv, const cplx<T>* B, cplx<T>* x, int ny) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cplx<T>* bs = reinterpret_cast<cplx<T>*>(sm_raw);
+  for (int c = threadIdx.x; c < ny; c += GV_THREADS) bs[c] = B[c];
+  __syncthreads();
+  gemv_n<T>(Dinv, bs, x, ny);
+}
+
+}  // namespace
+
+// ===================================================================== handle
+struct BcrHandle {
+  int prec;
+  int nx, ny;
+  std::vector<int64_t> n, m;      // rows / eliminated rows per level (index 0 = tridiagonal level)
+  std::vector<int64_t> off;       // store offsets (elements) of levels >= 1
+  int64_t final_off = 0;
+  int Lf = 1;                     // level with a single row
+  size_t esz = 0;                 // bytes per complex element
+  // factor storage
+  void *tdl = nullptr, *tdinv = nullptr, *tdu = nullptr, *tdu2 = nullptr;
+  uint8_t* tpiv = nullptr;
+  void* Dw[2] = {nullptr, nullptr};
+  void* Lw[2] = {nullptr, nullptr};
+  void* store = nullptr;
+  int32_t* status = nullptr;
+  size_t factor_bytes = 0;
+  Profiler* prof = nullptr;
+  // solve workspace (grown on demand)
+  int ws_nrhs = 0;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+};
+
+static void free_ws(BcrHandle* h) {
+  if (h->ws) cudaFree(h->ws);
+  h->ws = nullptr;
+  h->ws_nrhs = 0;
+  h->ws_bytes = 0;
+}
+
+void bcr_destroy(BcrHandle* h) {
+  if (!h) return;
+  void* ps[] = {h->tdl, h->tdinv, h->tdu, h->tdu2, h->tpiv, h->Dw[0], h->Dw[1],
+                h->Lw[0], h->Lw[1], h->store, h->status};
+  for (void* p : ps)
+    if (p) cudaFree(p);
+  free_ws(h);
+  delete h;
+}
+
+size_t bcr_bytes(const BcrHandle* h) { return h->factor_bytes + h->ws_bytes; }
+void bcr_set_profiler(BcrHandle* h, Profiler* p) { h->prof = p; }
+int bcr_precision(const BcrHandle* h) { return h->prec; }
+
+cudaError_t bcr_create(int nx, int ny, int prec, BcrHandle** out, size_t* bytes) {
+  *out = nullptr;
+  if (nx < 1 || ny < 2 || ny > 1024) return cudaErrorInvalidValue;
+  BcrHandle* h = new (std::nothrow) BcrHandle();
+  if (!h) return cudaErrorMemoryAllocation;
+  h->prec = prec;
+  h->nx = nx;
+  h->ny = ny;
+  h->esz = prec == RCI_FP64 ? sizeof(double2) : sizeof(float2);
+  const int64_t nn = (int64_t)ny * ny;
+  h->n.push_back(nx);
+  h->m.push_back(nx / 2);
+  int64_t cur = (nx + 1) / 2;
+  int64_t off = 0;
+  h->off.push_back(0);
+  int L = 1;
+  while (cur > 1) {
+    h->n.push_back(cur);
+    h->m.push_back(cur / 2);
+    h->off.push_back(off);
+    off += 3 * (cur / 2) * nn;
+    cur = (cur + 1) / 2;
+    ++L;
+  }
+  h->n.push_back(1);
+  h->m.push_back(0);
+  h->off.push_back(off);
+  h->Lf = L;
+  h->final_off = off;
+  int64_t store_elems = off + nn;
+  int64_t m0 = h->m[0], n1 = (nx + 1) / 2;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void** p, size_t b) {
+    if (e != cudaSuccess) return;
+    e = cudaMalloc(p, b < 16 ? 16 : b);
+    if (e == cudaSuccess) h->factor_bytes += b;
+  };
+  size_t m0b = (size_t)std::max<int64_t>(m0, 1) * ny;
+  alloc(&h->tdl, m0b * h->esz);
+  alloc(&h->tdinv, m0b * h->esz);
+  alloc(&h->tdu, m0b * h->esz);
+  alloc(&h->tdu2, m0b * h->esz);
+  alloc((void**)&h->tpiv, m0b);
+  for (int i = 0; i < 2; ++i) {
+    alloc(&h->Dw[i], (size_t)n1 * nn * h->esz);
+    alloc(&h->Lw[i], (size_t)n1 * nn * h->esz);
+  }
+  alloc(&h->store, (size_t)store_elems * h->esz);
+  alloc((void**)&h->status, sizeof(int32_t));
+  if (e != cudaSuccess) {
+    bcr_destroy(h);
+    return e;
+  }
+  *out = h;
+  if (bytes) *bytes = h->factor_bytes;
+  return cudaSuccess;
+}
+
+cudaError_t bcr_read_status(BcrHandle* h, int32_t* st, cudaStream_t s) {
+  RCI_CUDA_TRY(cudaMemcpyAsync(st, h->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  return cudaStreamSynchronize(s);
+}
+
+template <typename T>
+static cudaError_t factor_t(BcrHandle* h, const double2* dg, const double2* cx, const double2* cy,
+                            cudaStream_t s) {
+  const int nx = h->nx, ny = h->ny;
+  const int64_t nn = (int64_t)ny * ny;
+  const int m0 = (int)h->m[0];
+  const int n1 = (nx + 1) / 2;
+  RCI_CUDA_TRY(cudaMemsetAsync(h->status, 0, sizeof(int32_t), s));
+  auto tdl = (cplx<T>*)h->tdl;
+  auto tdinv = (cplx<T>*)h->tdinv;
+  auto tdu = (cplx<T>*)h->tdu;
+  auto tdu2 = (cplx<T>*)h->tdu2;
+  ProfScope* l0 = new ProfScope(h->prof, PF_LEVEL0, s, 48.0 * ny * (double)ny * n1,
+                                2.0 * n1 * (double)nn * sizeof(cplx<T>), 2);
+  if (m0 > 0) {
+    tri_factor_kernel<T><<<(unsigned)ceil_div(m0, 128), 128, 0, s>>>(dg, cy, nx, ny, m0, tdl, tdinv,
+                                                                    tdu, tdu2, h->tpiv, h->status); rci_note_launch();
+    RCI_CUDA_TRY(cudaGetLastError());
+  }
+  {
+    int thr = (int)ceil_div(ny, 32) * 32;
+    size_t smem = (size_t)13 * ny * sizeof(cplx<T>) + 2 * (size_t)ny;
+    if (smem > 48 * 1024)
+      RCI_CUDA_TRY(cudaFuncSetAttribute(level0_schur_kernel<T>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    level0_schur_kernel<T><<<n1, thr, smem, s>>>(dg, cx, cy, nx, ny, m0, tdl, tdinv, tdu, tdu2,
+                                                 h->tpiv, (cplx<T>*)h->Dw[0], (cplx<T>*)h->Lw[0]); rci_note_launch();
+    RCI_CUDA_TRY(cudaGetLastError());
+  }
+  delete l0;
+  const cplx<T> one = mkc(T(1), T(0)), mone = mkc(T(-1), T(0)), zero = czero<T>();
+  int cur = 0;
+  auto store = (cplx<T>*)h->store;
+  for (int l = 1; l < h->Lf; ++l) {
+    const int n = (int)h->n[l], m = (int)h->m[l], nk = (int)h->n[l + 1];
+    const int my = (n - 1) / 2;
+    cplx<T>* D = (cplx<T>*)h->Dw[cur];
+    cplx<T>* L = (cplx<T>*)h->Lw[cur];
+    cplx<T>* Dn = (cplx<T>*)h->Dw[1 - cur];
+    cplx<T>* Ln = (cplx<T>*)h->Lw[1 - cur];
+    cplx<T>* Dinv = store + h->off[l];
+    cplx<T>* X = Dinv + (int64_t)m * nn;
+    cplx<T>* Y = X + (int64_t)m * nn;
+    // D_r^{-1} for the odd rows (the working copy of D_r is destroyed)
+    {
+      ProfScope ps(h->prof, PF_INVERT, s, 8.0 * ny * (double)nn * m, 2.0 * m * nn * sizeof(cplx<T>), 1);
+      RCI_CUDA_TRY(launch_gj<T>(D + nn, 2 * nn, Dinv, nn, ny, m, h->status, s));
+    }
+    // X_k = Dinv_k L_{2k+1};  Y_k = Dinv_k L_{2k+2}^T
+    RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, false, one, Dinv, ny, nn, L + nn, ny, 2 * nn, zero,
+                         nullptr, 0, 0, X, ny, nn, m, s, h->prof));
+    RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, true, one, Dinv, ny, nn, L + 2 * nn, ny, 2 * nn, zero,
+                         nullptr, 0, 0, Y, ny, nn, my, s, h->prof));
+    // D'_0 = D_0;  D'_k = D_{2k} - L_{2k} Y_{k-1} (k >= 1);  D'_k -= L_{2k+1}^T X_k (k < m)
+    RCI_CUDA_TRY(cudaMemcpyAsync(Dn, D, nn * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s));
+    RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, false, mone, L + 2 * nn, ny, 2 * nn, Y, ny, nn, one,
+                         D + 2 * nn, ny, 2 * nn, Dn + nn, ny, nn, nk - 1, s, h->prof));
+    RCI_CUDA_TRY(gemm<T>(ny, ny, ny, true, false, mone, L + nn, ny, 2 * nn, X, ny, nn, one, Dn, ny,
+                         nn, Dn, ny, nn, m, s, h->prof));
+    // L'_k = -L_{2k} X_{k-1} (k >= 1)
+    RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, false, mone, L + 2 * nn, ny, 2 * nn, X, ny, nn, zero,
+                         nullptr, 0, 0, Ln + nn, ny, nn, nk - 1, s, h->prof));
+    cur = 1 - cur;
+  }
+  // last single row
+  {
+    ProfScope ps(h->prof, PF_INVERT, s, 8.0 * ny * (double)nn, 2.0 * nn * sizeof(cplx<T>), 1);
+    RCI_CUDA_TRY(launch_gj<T>((cplx<T>*)h->Dw[cur], 0, store + h->final_off, 0, ny, 1, h->status, s));
+  }
+  return cudaSuccess;
+}
+
+cudaError_t bcr_factor(BcrHandle* h, const double2* dg, const double2* cx, const double2* cy,
+                       cudaStream_t s) {
+  return h->prec == RCI_FP64 ? factor_t<double>(h, dg, cx, cy, s)
+                             : factor_t<float>(h, dg, cx, cy, s);
+}
+
+// workspace layout for nrhs right-hand sides (elements of cplx<T>):
+//   t0 [m0 row] | B_l [n_l row] (l = 1..Lf) | t_l [m_l row] (l = 1..Lf-1) | P, Q [m_1 row] | xf [row]
+static int64_t ws_elems(const BcrHandle* h, int nrhs) {
+  int64_t row = (int64_t)h->ny * nrhs;
+  int64_t tot = h->m[0] * row;
+  for (int l = 1; l <= h->Lf; ++l) tot += h->n[l] * row;
+  for (int l = 1; l < h->Lf; ++l) tot += h->m[l] * row;
+  int64_t m1 = h->Lf > 1 ? h->m[1] : 0;
+  tot += 2 * m1 * row + row;
+  return tot;
+}
+
+template <typename T>
+static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cplx<T>* x, int nrhs,
+                           cudaStream_t s) {
+  const int nx = h->nx, ny = h->ny;
+  const int64_t nn = (int64_t)ny * ny;
+  const int64_t row = (int64_t)ny * nrhs;
+  const int m0 = (int)h->m[0], n1 = (nx + 1) / 2;
+  if (h->ws_nrhs < nrhs) {
+    free_ws(h);
+    size_t bytes = (size_t)ws_elems(h, nrhs) * sizeof(cplx<T>);
+    RCI_CUDA_TRY(cudaMalloc(&h->ws, bytes));
+    h->ws_bytes = bytes;
+    h->ws_nrhs = nrhs;
+  }
+  // carve the workspace
+  cplx<T>* p = (cplx<T>*)h->ws;
+  cplx<T>* t0 = p;
+  p += h->m[0] * row;
+  std::vector<cplx<T>*> B(h->Lf + 1, nullptr), tl(h->Lf + 1, nullptr);
+  for (int l = 1; l <= h->Lf; ++l) {
+    B[l] = p;
+    p += h->n[l] * row;
+  }
+  for (int l = 1; l < h->Lf; ++l) {
+    tl[l] = p;
+    p += h->m[l] * row;
+  }
+  int64_t m1 = h->Lf > 1 ? h->m[1] : 0;
+  cplx<T>* P = p;
+  p += m1 * row;
+  cplx<T>* Q = p;
+  p += m1 * row;
+  cplx<T>* xf = p;
+
+  auto tdl = (const cplx<T>*)h->tdl;
+  auto tdinv = (const cplx<T>*)h->tdinv;
+  auto tdu = (const cplx<T>*)h->tdu;
+  auto tdu2 = (const cplx<T>*)h->tdu2;
+  auto store = (const cplx<T>*)h->store;
+  const cplx<T> one = mkc(T(1), T(0)), mone = mkc(T(-1), T(0)), zero = czero<T>();
+
+  double sbytes = 0.0, sflops = 0.0;
+  for (int l = 1; l < h->Lf; ++l) {
+    sbytes += 5.0 * h->m[l] * (double)nn * sizeof(cplx<T>);
+    sflops += 5.0 * 8.0 * h->m[l] * (double)nn * nrhs;
+  }
+  sbytes += (double)nn * sizeof(cplx<T>) + 2.0 * nx * (double)ny * nrhs * sizeof(cplx<T>);
+  ProfScope ps(h->prof, PF_SOLVE, s, sflops, sbytes, 0);
+  // ---- level 0 forward
+  if (m0 > 0) {
+    int64_t nt = (int64_t)m0 * nrhs;
+    fwd0_kernel<T><<<(unsigned)ceil_div(nt, 128), 128, 0, s>>>(b, t0, ny, m0, nrhs, tdl, tdinv,
+                                                                tdu, tdu2, h->tpiv); rci_note_launch();
+    RCI_CUDA_TRY(cudaGetLastError());
+  }
+  {
+    int64_t nt = (int64_t)n1 * row;
+    keep0_kernel<T><<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(b, t0, cx, B[1], nx, ny, n1, nrhs); rci_note_launch();
+    RCI_CUDA_TRY(cudaGetLastError());
+  }
+  // ---- dense levels forward
+  const int cmax8 = ny <= 256;
+  for (int l = 1; l < h->Lf; ++l) {
+    const int n = (int)h->n[l], m = (int)h->m[l], nk = (int)h->n[l + 1];
+    const int my = (n - 1) / 2;
+    const cplx<T>* Dinv = store + h->off[l];
+    const cplx<T>* X = Dinv + (int64_t)m * nn;
+    const cplx<T>* Y = X + (int64_t)m * nn;
+    if (nrhs == 1) {
+      size_t smem = (size_t)(1 + GV_WARPS) * ny * sizeof(cplx<T>);
+      if (cmax8) {
+        if (smem > 48 * 1024)
+          RCI_CUDA_TRY(cudaFuncSetAttribute(fwd_gemv_kernel<T, 8>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        fwd_gemv_kernel<T, 8><<<m, GV_THREADS, smem, s>>>(Dinv, X, Y, B[l], tl[l], P, Q, n, ny); rci_note_launch();
+      } else {
+        if (smem > 48 * 1024)
+          RCI_CUDA_TRY(cudaFuncSetAttribute(fwd_gemv_kernel<T, 32>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        fwd_gemv_kernel<T, 32><<<m, GV_THREADS, smem, s>>>(Dinv, X, Y, B[l], tl[l], P, Q, n, ny); rci_note_launch();
+      }
+      RCI_CUDA_TRY(cudaGetLastError());
+    } else {
+      const cplx<T>* Bodd = B[l] + row;
+      RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, one, Dinv, ny, nn, Bodd, nrhs, 2 * row, zero,
+                           nullptr, 0, 0, tl[l], nrhs, row, m, s));
+      RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, true, false, one, X, ny, nn, Bodd, nrhs, 2 * row, zero,
+                           nullptr, 0, 0, P, nrhs, row, m, s));
+      RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, true, false, one, Y, ny, nn, Bodd, nrhs, 2 * row, zero,
+                           nullptr, 0, 0, Q, nrhs, row, my, s));
+    }
+    int64_t nt = (int64_t)nk * row;
+    keep_kernel<T><<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(B[l], P, Q, B[l + 1], m, nk, row); rci_note_launch();
+    RCI_CUDA_TRY(cudaGetLastError());
+  }
+  // ---- single remaining row
+  {
+    const cplx<T>* Df = store + h->final_off;
+    if (nrhs == 1) {
+      final_gemv_kernel<T><<<1, GV_THREADS, ny * sizeof(cplx<T>), s>>>(Df, B[h->Lf], xf, ny); rci_note_launch();
+      RCI_CUDA_TRY(cudaGetLastError());
+    } else {
+      RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, one, Df, ny, 0, B[h->Lf], nrhs, 0, zero,
+                           nullptr, 0, 0, xf, nrhs, 0, 1, s));
+    }
+    RCI_CUDA_TRY(cudaMemcpyAsync(B[h->Lf], xf, row * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s));
+  }
+  // ---- dense levels backward (the solution of level l overwrites B[l])
+  for (int l = h->Lf - 1; l >= 1; --l) {
+    const int n = (int)h->n[l], m = (int)h->m[l], nk = (int)h->n[l + 1];
+    const int my = (n - 1) / 2;
+    const cplx<T>* Dinv = store + h->off[l];
+    const cplx<T>* X = Dinv + (int64_t)m * nn;
+    const cplx<T>* Y = X + (int64_t)m * nn;
+    if (nrhs == 1) {
+      bwd_gemv_kernel<T><<<nk, GV_THREADS, 2 * ny * sizeof(cplx<T>), s>>>(X, Y, tl[l], B[l + 1],
+                                                                          B[l], n, m, ny); rci_note_launch();
+      RCI_CUDA_TRY(cudaGetLastError());
+    } else {
+      int64_t nt = (int64_t)nk * row;
+      copy_kept_kernel<T><<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(B[l + 1], B[l], nk, row); rci_note_launch();
+      RCI_CUDA_TRY(cudaGetLastError());
+      RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, mone, X, ny, nn, B[l + 1], nrhs, row, one,
+                           tl[l], nrhs, row, B[l] + row, nrhs, 2 * row, m, s));
+      RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, mone, Y, ny, nn, B[l + 1] + row, nrhs, row,
+                           one, B[l] + row, nrhs, 2 * row, B[l] + row, nrhs, 2 * row, my, s));
+    }
+  }
+  // ---- level 0 backward
+  {
+    int64_t nt = (int64_t)n1 * nrhs;
+    bwd0_kernel<T><<<(unsigned)ceil_div(nt, 128), 128, 0, s>>>(b, B[1], cx, x, nx, ny, n1, nrhs,
+                                                                tdl, tdinv, tdu, tdu2, h->tpiv); rci_note_launch();
+    RCI_CUDA_TRY(cudaGetLastError());
+  }
+  return cudaSuccess;
+}
+
+cudaError_t bcr_solve(BcrHandle* h, const double2* cx, const void* b, void* x, int nrhs,
+                      cudaStream_t s) {
+  if (nrhs < 1) return cudaErrorInvalidValue;
+  if (h->prec == RCI_FP64)
+    return solve_t<double>(h, cx, (const double2*)b, (double2*)x, nrhs, s);
+  return solve_t<float>(h, cx, (const float2*)b, (float2*)x, nrhs, s);
+}

@@ -1,0 +1,40 @@
+// Block cyclic reduction (BCR) direct solver for the block-tridiagonal FDFD operator.
+//
+// A (ordered x-outermost) has nx block rows i with a tridiagonal ny x ny diagonal
+// block T_i and diagonal couplings diag(cx[i-1]) (to i-1) and diag(cx[i]) (to i+1).
+// A = A^T, so every reduced system stays symmetric and only the lower coupling L_i
+// (block (i, i-1)) is kept; the upper one is L_{i+1}^T.
+//
+// One reduction level eliminates the odd rows r of the current system:
+//   X_r = D_r^{-1} L_r,  Y_r = D_r^{-1} L_{r+1}^T
+//   kept row e:  D'_e = D_e - L_e Y_{e-1} - L_{e+1}^T X_{e+1},   L'_e = -L_e X_{e-1}
+// Solve, forward:  t_r = D_r^{-1} b_r,   b'_e = b_e - Y_{e-1}^T b_{e-1} - X_{e+1}^T b_{e+1}
+//        backward: x_r = t_r - X_r x_{r-1} - Y_r x_{r+1}.
+// Level 0 works on the tridiagonal T_i directly (pivoted tridiagonal LU, O(ny^2) per
+// row to form the dense Schur blocks); levels >= 1 use explicit inverses from a
+// pivoted Gauss-Jordan inversion and batched complex GEMMs.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+struct BcrHandle;
+
+// prec: RCI_FP64 -> double, RCI_FP32_REFINE -> float.  Allocates the factor store.
+cudaError_t bcr_create(int nx, int ny, int prec, BcrHandle** out, size_t* bytes);
+void bcr_destroy(BcrHandle* h);
+size_t bcr_bytes(const BcrHandle* h);
+
+// Factor from the FP64 coefficient arrays (dg, cx, cy as in assemble.cu).
+cudaError_t bcr_factor(BcrHandle* h, const double2* dg, const double2* cx, const double2* cy,
+                       cudaStream_t s);
+// Solve A x = b for nrhs right-hand sides, [i][j][q] with leading dimension nrhs, in the
+// handle's precision (float2 or double2 buffers).  b and x may alias.
+cudaError_t bcr_solve(BcrHandle* h, const double2* cx, const void* b, void* x, int nrhs,
+                      cudaStream_t s);
+// Device status word (DEV_OK / DEV_SINGULAR / DEV_NONFINITE), read synchronously.
+cudaError_t bcr_read_status(BcrHandle* h, int32_t* st, cudaStream_t s);
+int bcr_precision(const BcrHandle* h);
+// Optional profiler (owned by the caller) for the factor / solve kernel families.
+void bcr_set_profiler(BcrHandle* h, Profiler* p);

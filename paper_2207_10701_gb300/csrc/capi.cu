@@ -1,0 +1,778 @@
+// C ABI of the reciprocal incoherent-light evaluator (declarations and contracts in
+// include/rci.h).  Host code here only validates arguments, sequences kernels on the
+// grid's stream and moves scalars; every numerical step runs in the kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <atomic>
+
+#include "bcr.cuh"
+#include "kernels.cuh"
+
+static std::atomic<uint64_t> g_launches{0};
+void rci_note_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+struct rci_grid {
+  rci_grid_desc d{};
+  GridGeom g{};
+  cudaStream_t s = nullptr;
+  int device = 0;
+  int64_t N = 0;
+  // problem
+  double* widths = nullptr;
+  double* eps = nullptr;
+  double2 *dg = nullptr, *cx = nullptr, *cy = nullptr;
+  BcrHandle* bcr = nullptr;
+  bool has_design = false, factored = false;
+  // single right-hand-side vectors (FP64) and FP32 shadows
+  double2 *b1 = nullptr, *x1 = nullptr, *r1 = nullptr;
+  void *r32 = nullptr, *d32 = nullptr;
+  // objective row, source-plane field, lags, scalars
+  double2* crow = nullptr;
+  double2* vsrc = nullptr;
+  double* lags = nullptr;
+  double* qpart = nullptr;
+  double* dscal = nullptr;  // [0] qform, [1..] misc
+  double* part_r = nullptr;
+  double* part_b = nullptr;
+  double* ratio = nullptr;  // per-RHS residual ratio (up to MAXQ)
+  double* vf_scratch = nullptr;
+  int32_t* dstatus = nullptr;
+  // multi right-hand side buffers (grown on demand)
+  int mq_cap = 0;
+  double2 *mb = nullptr, *mx = nullptr, *mr = nullptr;
+  void *m32a = nullptr, *m32b = nullptr;
+  double *th_d = nullptr, *wq_d = nullptr, *f_d = nullptr;
+  int th_cap = 0;
+  // light cache
+  bool lags_valid = false;
+  rci_light lags_key{};
+  // settings
+  double tol32 = 1e-10, tol64 = 1e-13;
+  int max_refine32 = 12, max_refine64 = 2;
+  size_t bytes = 0;
+  cudaEvent_t ev[6] = {};
+  Profiler prof;
+  std::string err;
+};
+
+namespace {
+
+constexpr int MAXQ = 256;  // right-hand sides per multi-RHS chunk
+
+rci_status fail(rci_grid* g, rci_status st, const std::string& msg) {
+  if (g) g->err = msg;
+  return st;
+}
+
+rci_status cuda_fail(rci_grid* g, cudaError_t e, const char* where) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(g, RCI_ENOMEM, std::string(where) + ": device allocation failed");
+  return fail(g, RCI_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(expr, where)                                  \
+  do {                                                   \
+    cudaError_t _e = (expr);                             \
+    if (_e != cudaSuccess) return cuda_fail(g, _e, where); \
+  } while (0)
+
+template <typename P>
+cudaError_t dalloc(rci_grid* g, P** p, size_t bytes) {
+  cudaError_t e = cudaMalloc((void**)p, bytes < 16 ? 16 : bytes);
+  if (e == cudaSuccess) g->bytes += bytes;
+  return e;
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+bool desc_ok(const rci_grid_desc* d, std::string& why) {
+  if (d->n_cells < 1 || d->cell_px < 1 || d->ppl < 2 || d->npml < 1 || d->ny < 4) {
+    why = "counts must be positive (n_cells, cell_px, npml >= 1, ppl >= 2, ny >= 4)";
+    return false;
+  }
+  if (d->rows_sub < 1 || d->rows_pillar < 1 || d->src_offset < 0 || d->src_offset >= d->rows_sub) {
+    why = "rows_sub, rows_pillar >= 1 and 0 <= src_offset < rows_sub required";
+    return false;
+  }
+  if (d->ny - 2 * d->npml - d->rows_sub - d->rows_pillar < 1) {
+    why = "ny leaves no air rows above the pillars";
+    return false;
+  }
+  if (d->ny > 1024) {
+    why = "ny > 1024 is not supported";
+    return false;
+  }
+  if (!(d->eps_pillar > 0 && d->eps_sub > 0 && d->eps_air > 0) || !(d->pml_R0 > 0 && d->pml_R0 < 1) ||
+      d->pml_m < 0) {
+    why = "permittivities must be positive, 0 < pml_R0 < 1, pml_m >= 0";
+    return false;
+  }
+  if (d->prec != RCI_FP64 && d->prec != RCI_FP32_REFINE) {
+    why = "unknown precision";
+    return false;
+  }
+  int64_t nx = (int64_t)d->n_cells * d->cell_px + 2 * (int64_t)d->npml;
+  if (nx > (1 << 22)) {
+    why = "grid too wide";
+    return false;
+  }
+  return true;
+}
+
+GridGeom make_geom(const rci_grid_desc& d) {
+  GridGeom g{};
+  g.nx = d.n_cells * d.cell_px + 2 * d.npml;
+  g.ny = d.ny;
+  g.npml = d.npml;
+  g.n_src = g.nx - 2 * d.npml;
+  g.j_src = d.npml + d.src_offset;
+  g.j_p0 = d.npml + d.rows_sub;
+  g.j_p1 = g.j_p0 + d.rows_pillar;
+  g.n_cells = d.n_cells;
+  g.cell_px = d.cell_px;
+  g.h = 1.0 / d.ppl;
+  g.k0 = 2.0 * M_PI;
+  g.k_sub = g.k0 * std::sqrt(d.eps_sub);
+  g.eps_pillar = d.eps_pillar;
+  g.eps_sub = d.eps_sub;
+  g.eps_air = d.eps_air;
+  double dd = d.npml * g.h;
+  g.sigma_max = -(d.pml_m + 1) * std::log(d.pml_R0) / (2.0 * dd);
+  g.width = g.n_src * g.h;
+  g.pml_m = d.pml_m;
+  return g;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+bool light_eq(const rci_light& a, const rci_light& b) {
+  return a.kind == b.kind && a.c == b.c && a.th1 == b.th1 && a.th2 == b.th2 && a.lags == b.lags;
+}
+
+rci_status check_light(rci_grid* g, const rci_light* L) {
+  if (!L) return fail(g, RCI_EINVAL, "light is NULL");
+  if (L->kind == RCI_LIGHT_CONE) {
+    if (!(L->c > 0 && L->c < M_PI / 2)) return fail(g, RCI_EINVAL, "cone half-angle must be in (0, pi/2)");
+  } else if (L->kind == RCI_LIGHT_ANNULUS) {
+    if (!(L->th1 >= 0 && L->th1 < L->th2 && L->th2 < M_PI / 2))
+      return fail(g, RCI_EINVAL, "annulus needs 0 <= th1 < th2 < pi/2");
+  } else if (L->kind == RCI_LIGHT_USER_LAGS) {
+    if (!L->lags) return fail(g, RCI_EINVAL, "user lags pointer is NULL");
+  } else {
+    return fail(g, RCI_EINVAL, "unknown light kind");
+  }
+  return RCI_OK;
+}
+
+rci_status ensure_lags(rci_grid* g, const rci_light* L) {
+  rci_status st = check_light(g, L);
+  if (st != RCI_OK) return st;
+  if (L->kind == RCI_LIGHT_USER_LAGS) {
+    CK(cudaMemcpyAsync(g->lags, L->lags, sizeof(double) * g->g.n_src, cudaMemcpyHostToDevice, g->s),
+       "copy lags");
+    g->lags_valid = false;
+    return RCI_OK;
+  }
+  if (g->lags_valid && light_eq(g->lags_key, *L)) return RCI_OK;
+  CK(launch_w_lags(L->kind, L->c, L->th1, L->th2, g->g.k_sub, g->g.h, g->g.n_src, g->lags, g->s),
+     "W lags");
+  g->lags_key = *L;
+  g->lags_valid = true;
+  return RCI_OK;
+}
+
+// conj(w) as a full-grid right-hand side in b (zeroed first).  The objective row is kept
+// in g->crow for the brute-force projection.
+rci_status build_objective(rci_grid* g, const rci_objective* o, double2* b) {
+  const GridGeom& G = g->g;
+  if (!o) return fail(g, RCI_EINVAL, "objective is NULL");
+  CK(cudaMemsetAsync(b, 0, sizeof(double2) * g->N, g->s), "zero rhs");
+  if (o->kind == RCI_OBJ_POINT) {
+    if (o->i_f < 0 || o->i_f >= G.nx || o->j_f < 0 || o->j_f >= G.ny)
+      return fail(g, RCI_EINVAL, "focus node outside the grid");
+    double2 one = make_double2(1.0, 0.0);
+    CK(cudaMemcpyAsync(b + (int64_t)o->i_f * G.ny + o->j_f, &one, sizeof(double2),
+                       cudaMemcpyHostToDevice, g->s),
+       "point source");
+    CK(cudaStreamSynchronize(g->s), "point source");
+    return RCI_OK;
+  }
+  if (o->monitor_row < 0 || o->monitor_row >= G.ny)
+    return fail(g, RCI_EINVAL, "monitor row outside the grid");
+  if (o->kind == RCI_OBJ_PLANEWAVE) {
+    if (!(std::fabs(o->theta_out) < M_PI / 2)) return fail(g, RCI_EINVAL, "theta_out out of range");
+    CK(launch_planewave_row(G, o->theta_out, g->crow, g->s), "planewave objective");
+  } else if (o->kind == RCI_OBJ_VIRTUAL_FOCUS) {
+    if (o->d_rows < 0) return fail(g, RCI_EINVAL, "d_rows must be >= 0");
+    CK(launch_virtual_focus_row(G, o->x_f, o->d_rows, g->crow, g->vf_scratch, g->s),
+       "virtual focus objective");
+  } else if (o->kind == RCI_OBJ_USER_ROW) {
+    if (!o->w_row) return fail(g, RCI_EINVAL, "w_row is NULL");
+    CK(cudaMemcpyAsync(g->crow, o->w_row, sizeof(double2) * G.n_src, cudaMemcpyHostToDevice, g->s),
+       "user objective");
+    CK(launch_conj(g->crow, G.n_src, g->s), "user objective");
+  } else {
+    return fail(g, RCI_EINVAL, "unknown objective kind");
+  }
+  CK(launch_scatter_row(G, g->crow, o->monitor_row, b, g->s), "objective rhs");
+  return RCI_OK;
+}
+
+rci_status ensure_multi(rci_grid* g, int nq) {
+  if (g->mq_cap >= nq) return RCI_OK;
+  dfree(g->mb);
+  dfree(g->mx);
+  dfree(g->mr);
+  dfree(g->m32a);
+  dfree(g->m32b);
+  g->mb = g->mx = g->mr = nullptr;
+  g->m32a = g->m32b = nullptr;
+  size_t n = (size_t)g->N * nq;
+  CK(dalloc(g, &g->mb, n * sizeof(double2)), "multi-rhs buffers");
+  CK(dalloc(g, &g->mx, n * sizeof(double2)), "multi-rhs buffers");
+  CK(dalloc(g, &g->mr, n * sizeof(double2)), "multi-rhs buffers");
+  if (g->d.prec == RCI_FP32_REFINE) {
+    CK(dalloc(g, &g->m32a, n * sizeof(float2)), "multi-rhs buffers");
+    CK(dalloc(g, &g->m32b, n * sizeof(float2)), "multi-rhs buffers");
+  }
+  g->mq_cap = nq;
+  return RCI_OK;
+}
+
+// Residual r = b - A x (FP64 stencil) and the largest ||r||/||b|| over the columns.
+rci_status residual_ratio(rci_grid* g, const double2* b, const double2* x, double2* r, int nrhs,
+                          double* worst) {
+  int nblk = residual_blocks(g->g);
+  {
+    ProfScope ps(&g->prof, PF_RESIDUAL, g->s, 18.0 * g->N * nrhs,
+                 (double)g->N * (48.0 + 48.0 * nrhs), 2);
+    CK(launch_residual(g->g, g->dg, g->cx, g->cy, b, x, r, nrhs, g->part_r, g->part_b, g->s),
+       "residual");
+    CK(launch_ratio_norms(g->part_r, g->part_b, nblk, nrhs, g->ratio, g->s), "residual norms");
+  }
+  std::vector<double> h(nrhs);
+  CK(cudaMemcpyAsync(h.data(), g->ratio, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, g->s),
+     "residual norms");
+  CK(cudaStreamSynchronize(g->s), "residual norms");
+  double w = 0.0;
+  for (double v : h) {
+    if (!std::isfinite(v)) {
+      *worst = v;
+      return fail(g, RCI_ENUMERIC, "non-finite residual");
+    }
+    w = v > w ? v : w;
+  }
+  *worst = w;
+  return RCI_OK;
+}
+
+// Solve A x = b (FP64 in/out, device, nrhs columns) with the grid's factorisation and
+// iterative refinement on the FP64 stencil residual.  r, a32, b32 are scratch buffers of
+// the same size (a32/b32 complex64, only for FP32 grids).
+rci_status refined_solve(rci_grid* g, const double2* b, double2* x, double2* r, void* a32,
+                         void* b32, int nrhs, rci_info* info) {
+  const int64_t n = g->N * nrhs;
+  double worst = 0.0;
+  int it = 0;
+  rci_status st = RCI_OK;
+  if (g->d.prec == RCI_FP64) {
+    CK(bcr_solve(g->bcr, g->cx, b, x, nrhs, g->s), "solve");
+    st = residual_ratio(g, b, x, r, nrhs, &worst);
+    if (st != RCI_OK) return st;
+    while (worst > g->tol64 && it < g->max_refine64) {
+      CK(bcr_solve(g->bcr, g->cx, r, r, nrhs, g->s), "refine solve");
+      CK(launch_axpy64(x, r, n, g->s), "refine update");
+      ++it;
+      st = residual_ratio(g, b, x, r, nrhs, &worst);
+      if (st != RCI_OK) return st;
+    }
+  } else {
+    CK(cudaMemsetAsync(x, 0, sizeof(double2) * n, g->s), "zero x");
+    CK(cudaMemcpyAsync(r, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, g->s), "copy b");
+    worst = 1.0;
+    while (true) {
+      CK(launch_to_f32(r, (float2*)a32, n, g->s), "to fp32");
+      CK(bcr_solve(g->bcr, g->cx, a32, b32, nrhs, g->s), "fp32 solve");
+      CK(launch_add_f32(x, (const float2*)b32, n, g->s), "update");
+      ++it;
+      st = residual_ratio(g, b, x, r, nrhs, &worst);
+      if (st != RCI_OK) return st;
+      if (worst <= g->tol32 || it >= g->max_refine32) break;
+    }
+    it -= 1;  // the first FP32 solve is not a refinement step
+  }
+  if (info) {
+    info->refine_iters = it;
+    info->rel_residual = worst;
+  }
+  double tol = g->d.prec == RCI_FP64 ? 1e-9 : g->tol32;
+  if (worst > tol) return fail(g, RCI_ENOCONV, "iterative refinement did not converge");
+  return RCI_OK;
+}
+
+rci_status reciprocal_solve(rci_grid* g, const rci_objective* o, rci_info* info) {
+  if (!g->factored) return fail(g, RCI_ESTATE, "grid is not factored");
+  rci_status st = build_objective(g, o, g->b1);
+  if (st != RCI_OK) return st;
+  CK(cudaEventRecord(g->ev[2], g->s), "event");
+  st = refined_solve(g, g->b1, g->x1, g->r1, g->r32, g->d32, 1, info);
+  CK(cudaEventRecord(g->ev[3], g->s), "event");
+  if (st != RCI_OK && st != RCI_ENOCONV) return st;
+  CK(launch_gather_source_row(g->g, g->x1, g->vsrc, g->s), "gather v");
+  if (info) {
+    float ms = 0;
+    cudaEventSynchronize(g->ev[3]);
+    cudaEventElapsedTime(&ms, g->ev[2], g->ev[3]);
+    info->ms_solve = ms;
+  }
+  return st;
+}
+
+rci_status run_angles(rci_grid* g, const rci_objective* o, const double* th_dev,
+                      const double* wq_dev, int nq, double* f_dev, rci_info* info) {
+  const GridGeom& G = g->g;
+  // objective row / point (reuses the reciprocal builder for validation and crow)
+  rci_status st = build_objective(g, o, g->b1);
+  if (st != RCI_OK) return st;
+  int chunk = nq < MAXQ ? nq : MAXQ;
+  st = ensure_multi(g, chunk);
+  if (st != RCI_OK) return st;
+  int worst_it = 0;
+  double worst_res = 0.0;
+  rci_status agg = RCI_OK;
+  for (int q0 = 0; q0 < nq; q0 += chunk) {
+    int c = nq - q0 < chunk ? nq - q0 : chunk;
+    CK(cudaMemsetAsync(g->mb, 0, sizeof(double2) * g->N * c, g->s), "zero sources");
+    CK(launch_sources(G, th_dev + q0, c, c, g->mb, g->s), "sources");
+    rci_info ci{};
+    st = refined_solve(g, g->mb, g->mx, g->mr, g->m32a, g->m32b, c, &ci);
+    if (st != RCI_OK && st != RCI_ENOCONV) return st;
+    if (st == RCI_ENOCONV) agg = st;
+    worst_it = ci.refine_iters > worst_it ? ci.refine_iters : worst_it;
+    worst_res = ci.rel_residual > worst_res ? ci.rel_residual : worst_res;
+    if (o->kind == RCI_OBJ_POINT) {
+      CK(launch_project_point(G, o->i_f, o->j_f, g->mx, c, c, f_dev + q0, g->s), "project");
+    } else {
+      CK(launch_project_row(G, g->crow, o->monitor_row, g->mx, c, c, f_dev + q0, g->s), "project");
+    }
+  }
+  (void)wq_dev;
+  if (info) {
+    info->refine_iters = worst_it;
+    info->rel_residual = worst_res;
+  }
+  return agg;
+}
+
+rci_status ensure_theta(rci_grid* g, int nq) {
+  if (g->th_cap >= nq) return RCI_OK;
+  dfree(g->th_d);
+  dfree(g->wq_d);
+  dfree(g->f_d);
+  g->th_d = g->wq_d = g->f_d = nullptr;
+  CK(dalloc(g, &g->th_d, sizeof(double) * nq), "angles");
+  CK(dalloc(g, &g->wq_d, sizeof(double) * nq), "angles");
+  CK(dalloc(g, &g->f_d, sizeof(double) * nq), "angles");
+  g->th_cap = nq;
+  return RCI_OK;
+}
+
+rci_status finish_angles(rci_grid* g, int nq, double* fom, double* avg) {
+  if (fom)
+    CK(cudaMemcpyAsync(fom, g->f_d, sizeof(double) * nq, cudaMemcpyDeviceToHost, g->s), "fom copy");
+  CK(launch_weighted_sum(g->wq_d, g->f_d, nq, g->dscal + 1, g->s), "weighted sum");
+  double a = 0.0;
+  CK(cudaMemcpyAsync(&a, g->dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, g->s), "avg copy");
+  CK(cudaStreamSynchronize(g->s), "avg copy");
+  if (g->prof.on) g->prof.collect();
+  if (!std::isfinite(a)) return fail(g, RCI_ENUMERIC, "non-finite brute-force average");
+  if (avg) *avg = a;
+  return RCI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rci_status_str(rci_status s) {
+  switch (s) {
+    case RCI_OK: return "ok";
+    case RCI_EINVAL: return "invalid argument";
+    case RCI_ENOMEM: return "out of device memory";
+    case RCI_ECUDA: return "CUDA error";
+    case RCI_ESTATE: return "call out of order";
+    case RCI_ESINGULAR: return "singular diagonal block";
+    case RCI_ENOCONV: return "iterative refinement did not converge";
+    case RCI_ENUMERIC: return "non-finite value";
+    case RCI_ETIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+const char* rci_last_error(const rci_grid* g) { return g ? g->err.c_str() : ""; }
+
+rci_status rci_destroy_grid(rci_grid* g) {
+  if (!g) return RCI_OK;
+  DeviceGuard dg(g->device);
+  if (g->s) cudaStreamSynchronize(g->s);
+  void* ps[] = {g->widths, g->eps, g->dg, g->cx, g->cy, g->b1, g->x1, g->r1, g->r32, g->d32,
+                g->crow, g->vsrc, g->lags, g->qpart, g->dscal, g->part_r, g->part_b, g->ratio,
+                g->vf_scratch, g->dstatus, g->mb, g->mx, g->mr, g->m32a, g->m32b, g->th_d,
+                g->wq_d, g->f_d};
+  for (void* p : ps) dfree(p);
+  bcr_destroy(g->bcr);
+  if (g->prof.pool) {
+    for (int i = 0; i < g->prof.cap; ++i) cudaEventDestroy(g->prof.pool[i]);
+    delete[] g->prof.pool;
+    delete[] g->prof.recs;
+  }
+  for (cudaEvent_t e : g->ev)
+    if (e) cudaEventDestroy(e);
+  delete g;
+  return RCI_OK;
+}
+
+rci_status rci_create_grid(const rci_grid_desc* desc, void* stream, rci_grid** out) {
+  if (!desc || !out) return RCI_EINVAL;
+  *out = nullptr;
+  std::string why;
+  if (!desc_ok(desc, why)) return RCI_EINVAL;
+  rci_grid* g = new (std::nothrow) rci_grid();
+  if (!g) return RCI_ENOMEM;
+  g->d = *desc;
+  g->g = make_geom(*desc);
+  g->s = (cudaStream_t)stream;
+  g->device = desc->device;
+  g->N = (int64_t)g->g.nx * g->g.ny;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || desc->device < 0 || desc->device >= ndev) {
+    delete g;
+    return RCI_ECUDA;
+  }
+  DeviceGuard guard(g->device);
+  auto bail = [&](rci_status st) {
+    rci_destroy_grid(g);
+    return st;
+  };
+#define CKC(expr)                                                             \
+  do {                                                                        \
+    cudaError_t _e = (expr);                                                  \
+    if (_e != cudaSuccess)                                                    \
+      return bail(_e == cudaErrorMemoryAllocation ? RCI_ENOMEM : RCI_ECUDA);  \
+  } while (0)
+  const int64_t N = g->N, ns = g->g.n_src;
+  CKC(dalloc(g, &g->widths, sizeof(double) * desc->n_cells));
+  CKC(dalloc(g, &g->eps, sizeof(double) * N));
+  CKC(dalloc(g, &g->dg, sizeof(double2) * N));
+  CKC(dalloc(g, &g->cx, sizeof(double2) * N));
+  CKC(dalloc(g, &g->cy, sizeof(double2) * N));
+  CKC(dalloc(g, &g->b1, sizeof(double2) * N));
+  CKC(dalloc(g, &g->x1, sizeof(double2) * N));
+  CKC(dalloc(g, &g->r1, sizeof(double2) * N));
+  if (desc->prec == RCI_FP32_REFINE) {
+    CKC(dalloc(g, &g->r32, sizeof(float2) * N));
+    CKC(dalloc(g, &g->d32, sizeof(float2) * N));
+  }
+  CKC(dalloc(g, &g->crow, sizeof(double2) * ns));
+  CKC(dalloc(g, &g->vsrc, sizeof(double2) * ns));
+  CKC(dalloc(g, &g->lags, sizeof(double) * ns));
+  CKC(dalloc(g, &g->qpart, sizeof(double) * qform_num_partials(ns)));
+  CKC(dalloc(g, &g->dscal, sizeof(double) * 8));
+  CKC(dalloc(g, &g->part_r, sizeof(double) * residual_blocks(g->g) * MAXQ));
+  CKC(dalloc(g, &g->part_b, sizeof(double) * residual_blocks(g->g) * MAXQ));
+  CKC(dalloc(g, &g->ratio, sizeof(double) * MAXQ));
+  CKC(dalloc(g, &g->vf_scratch, sizeof(double) * (2 * VF_ORDER + 6 * VF_NODES)));
+  CKC(dalloc(g, &g->dstatus, sizeof(int32_t)));
+  CKC(cudaMemsetAsync(g->cx, 0, sizeof(double2) * N, g->s));
+  for (auto& e : g->ev) CKC(cudaEventCreate(&e));
+  size_t fb = 0;
+  CKC(bcr_create(g->g.nx, g->g.ny, desc->prec, &g->bcr, &fb));
+  g->bytes += fb;
+  CKC(cudaStreamSynchronize(g->s));
+#undef CKC
+  *out = g;
+  return RCI_OK;
+}
+
+rci_status rci_grid_query(const rci_grid* g, int64_t* nx, int64_t* ny, int64_t* n_src,
+                          size_t* device_bytes) {
+  if (!g) return RCI_EINVAL;
+  if (nx) *nx = g->g.nx;
+  if (ny) *ny = g->g.ny;
+  if (n_src) *n_src = g->g.n_src;
+  if (device_bytes) *device_bytes = g->bytes + (g->bcr ? bcr_bytes(g->bcr) : 0);
+  return RCI_OK;
+}
+
+rci_status rci_set_design(rci_grid* g, const double* widths, int64_t n_cells, int on_device) {
+  if (!g) return RCI_EINVAL;
+  if (!widths) return fail(g, RCI_EINVAL, "widths is NULL");
+  if (n_cells != g->d.n_cells) return fail(g, RCI_EINVAL, "need one width per cell");
+  DeviceGuard dg(g->device);
+  if (!on_device) {
+    // host widths are checked here; device widths are checked by the raster kernel and
+    // reported by the next rci_factor (no device-to-host round trip on that path)
+    const double period = g->d.cell_px * g->g.h;
+    for (int64_t m = 0; m < n_cells; ++m)
+      if (!(widths[m] > 0.0 && widths[m] < period))
+        return fail(g, RCI_EINVAL, "each width must lie in (0, period)");
+  }
+  CK(cudaMemsetAsync(g->dstatus, 0, sizeof(int32_t), g->s), "status");
+  CK(cudaMemcpyAsync(g->widths, widths, sizeof(double) * n_cells,
+                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->s),
+     "widths");
+  {
+    ProfScope ps(&g->prof, PF_SETUP, g->s, 0.0, 64.0 * g->N, 2);
+    CK(launch_raster_eps(g->g, g->widths, g->eps, g->dstatus, g->s), "raster");
+    CK(launch_assemble(g->g, g->eps, g->dg, g->cx, g->cy, g->s), "assemble");
+  }
+  g->has_design = true;
+  g->factored = false;
+  return RCI_OK;
+}
+
+rci_status rci_factor(rci_grid* g) {
+  if (!g) return RCI_EINVAL;
+  if (!g->has_design) return fail(g, RCI_ESTATE, "no design set");
+  DeviceGuard dg(g->device);
+  CK(cudaEventRecord(g->ev[0], g->s), "event");
+  CK(bcr_factor(g->bcr, g->dg, g->cx, g->cy, g->s), "factor");
+  CK(cudaEventRecord(g->ev[1], g->s), "event");
+  int32_t st = 0, sd = 0;
+  CK(cudaMemcpyAsync(&sd, g->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, g->s), "status");
+  CK(bcr_read_status(g->bcr, &st, g->s), "factor status");
+  if (g->prof.on) g->prof.collect();
+  if (sd == DEV_BADINPUT) {
+    g->has_design = false;
+    return fail(g, RCI_EINVAL, "a device width lies outside (0, period)");
+  }
+  if (st == DEV_SINGULAR) return fail(g, RCI_ESINGULAR, "zero pivot in a diagonal block");
+  g->factored = true;
+  return RCI_OK;
+}
+
+rci_status rci_solve(rci_grid* g, const double* b, double* x, int64_t nrhs, rci_info* info) {
+  if (!g) return RCI_EINVAL;
+  if (!b || !x || nrhs < 1 || nrhs > MAXQ) return fail(g, RCI_EINVAL, "bad solve arguments (1 <= nrhs <= 256)");
+  if (!g->factored) return fail(g, RCI_ESTATE, "grid is not factored");
+  DeviceGuard dg(g->device);
+  rci_status st;
+  if (nrhs == 1) {
+    CK(cudaMemcpyAsync(g->b1, b, sizeof(double2) * g->N, cudaMemcpyDeviceToDevice, g->s), "copy b");
+    st = refined_solve(g, g->b1, g->x1, g->r1, g->r32, g->d32, 1, info);
+    CK(cudaMemcpyAsync(x, g->x1, sizeof(double2) * g->N, cudaMemcpyDeviceToDevice, g->s), "copy x");
+  } else {
+    st = ensure_multi(g, (int)nrhs);
+    if (st != RCI_OK) return st;
+    CK(cudaMemcpyAsync(g->mb, b, sizeof(double2) * g->N * nrhs, cudaMemcpyDeviceToDevice, g->s),
+       "copy b");
+    st = refined_solve(g, g->mb, g->mx, g->mr, g->m32a, g->m32b, (int)nrhs, info);
+    CK(cudaMemcpyAsync(x, g->mx, sizeof(double2) * g->N * nrhs, cudaMemcpyDeviceToDevice, g->s),
+       "copy x");
+  }
+  CK(cudaStreamSynchronize(g->s), "solve");
+  if (g->prof.on) g->prof.collect();
+  return st;
+}
+
+rci_status rci_solve_reciprocal(rci_grid* g, const rci_objective* obj, double* v_src_out,
+                                double* v_full_out, rci_info* info) {
+  if (!g) return RCI_EINVAL;
+  DeviceGuard dg(g->device);
+  rci_status st = reciprocal_solve(g, obj, info);
+  if (st != RCI_OK && st != RCI_ENOCONV) return st;
+  if (v_src_out)
+    CK(cudaMemcpyAsync(v_src_out, g->vsrc, sizeof(double2) * g->g.n_src, cudaMemcpyDeviceToDevice,
+                       g->s),
+       "copy v");
+  if (v_full_out) {
+    CK(cudaMemcpyAsync(v_full_out, g->x1, sizeof(double2) * g->N, cudaMemcpyDeviceToDevice, g->s),
+       "copy v");
+    CK(launch_conj((double2*)v_full_out, g->N, g->s), "conj v");
+  }
+  CK(cudaStreamSynchronize(g->s), "reciprocal");
+  return st;
+}
+
+rci_status rci_avg_intensity(rci_grid* g, const rci_objective* obj, const rci_light* light,
+                             double* out, rci_info* info) {
+  if (!g) return RCI_EINVAL;
+  if (!out) return fail(g, RCI_EINVAL, "out is NULL");
+  DeviceGuard dg(g->device);
+  rci_status st = check_light(g, light);
+  if (st != RCI_OK) return st;
+  rci_status sst = reciprocal_solve(g, obj, info);
+  if (sst != RCI_OK && sst != RCI_ENOCONV) return sst;
+  st = ensure_lags(g, light);
+  if (st != RCI_OK) return st;
+  CK(cudaEventRecord(g->ev[4], g->s), "event");
+  {
+    const double n = (double)g->g.n_src;
+    ProfScope ps(&g->prof, PF_QFORM, g->s, 2.0 * n * n, 24.0 * n, 2);
+    CK(launch_qform(g->vsrc, g->lags, g->g.n_src, g->qpart, g->dscal, g->s), "qform");
+  }
+  CK(cudaEventRecord(g->ev[5], g->s), "event");
+  double F = 0.0;
+  CK(cudaMemcpyAsync(&F, g->dscal, sizeof(double), cudaMemcpyDeviceToHost, g->s), "qform copy");
+  CK(cudaStreamSynchronize(g->s), "qform");
+  if (g->prof.on) g->prof.collect();
+  if (!std::isfinite(F)) return fail(g, RCI_ENUMERIC, "non-finite averaged intensity");
+  *out = F;
+  if (info) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, g->ev[4], g->ev[5]);
+    info->ms_qform = ms;
+    cudaEventElapsedTime(&ms, g->ev[0], g->ev[1]);
+    info->ms_factor = ms;
+  }
+  return sst;
+}
+
+rci_status rci_solve_angles(rci_grid* g, const rci_objective* obj, const double* theta,
+                            const double* weight, int64_t nq, double* fom_per_angle,
+                            double* avg_out, rci_info* info) {
+  if (!g) return RCI_EINVAL;
+  if (!theta || !weight || nq < 1 || nq > (1 << 20)) return fail(g, RCI_EINVAL, "bad angle arguments");
+  if (!g->factored) return fail(g, RCI_ESTATE, "grid is not factored");
+  for (int64_t q = 0; q < nq; ++q)
+    if (!(std::fabs(theta[q]) < M_PI / 2)) return fail(g, RCI_EINVAL, "angles must lie in (-pi/2, pi/2)");
+  DeviceGuard dg(g->device);
+  rci_status st = ensure_theta(g, (int)nq);
+  if (st != RCI_OK) return st;
+  CK(cudaMemcpyAsync(g->th_d, theta, sizeof(double) * nq, cudaMemcpyHostToDevice, g->s), "angles");
+  CK(cudaMemcpyAsync(g->wq_d, weight, sizeof(double) * nq, cudaMemcpyHostToDevice, g->s), "angles");
+  rci_status rs = run_angles(g, obj, g->th_d, g->wq_d, (int)nq, g->f_d, info);
+  if (rs != RCI_OK && rs != RCI_ENOCONV) return rs;
+  st = finish_angles(g, (int)nq, fom_per_angle, avg_out);
+  return st != RCI_OK ? st : rs;
+}
+
+rci_status rci_avg_bruteforce(rci_grid* g, const rci_objective* obj, const rci_light* light,
+                              int64_t nq, double* fom_per_angle, double* avg_out, rci_info* info) {
+  if (!g) return RCI_EINVAL;
+  if (!g->factored) return fail(g, RCI_ESTATE, "grid is not factored");
+  rci_status st = check_light(g, light);
+  if (st != RCI_OK) return st;
+  if (light->kind == RCI_LIGHT_USER_LAGS) return fail(g, RCI_EINVAL, "brute force needs a cone or an annulus");
+  if (nq < 1 || nq > (1 << 20) || (light->kind == RCI_LIGHT_ANNULUS && nq % 2))
+    return fail(g, RCI_EINVAL, "bad number of angles (even for an annulus)");
+  DeviceGuard dg(g->device);
+  st = ensure_theta(g, (int)nq);
+  if (st != RCI_OK) return st;
+  CK(launch_light_rule(light->kind, light->c, light->th1, light->th2, (int)nq, g->th_d, g->wq_d,
+                       g->s),
+     "quadrature rule");
+  rci_status rs = run_angles(g, obj, g->th_d, g->wq_d, (int)nq, g->f_d, info);
+  if (rs != RCI_OK && rs != RCI_ENOCONV) return rs;
+  st = finish_angles(g, (int)nq, fom_per_angle, avg_out);
+  return st != RCI_OK ? st : rs;
+}
+
+rci_status rci_qform_toeplitz(const double* v, const double* lags, int64_t n, double* out,
+                              void* stream) {
+  if (!v || !lags || !out || n < 1 || n > (1LL << 31)) return RCI_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* part = nullptr;
+  double* dout = nullptr;
+  size_t np = (size_t)qform_num_partials(n);
+  if (cudaMalloc(&part, sizeof(double) * np) != cudaSuccess) return RCI_ENOMEM;
+  if (cudaMalloc(&dout, sizeof(double)) != cudaSuccess) {
+    cudaFree(part);
+    return RCI_ENOMEM;
+  }
+  rci_status st = RCI_OK;
+  double F = 0.0;
+  if (launch_qform((const double2*)v, lags, n, part, dout, s) != cudaSuccess ||
+      cudaMemcpyAsync(&F, dout, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    st = RCI_ECUDA;
+  cudaFree(part);
+  cudaFree(dout);
+  if (st == RCI_OK) {
+    if (!std::isfinite(F)) return RCI_ENUMERIC;
+    *out = F;
+  }
+  return st;
+}
+
+rci_status rci_gauss_legendre(int64_t n, double a, double b, double* nodes, double* weights,
+                              void* stream) {
+  if (n < 1 || n > (1 << 20) || !nodes || !weights) return RCI_EINVAL;
+  cudaError_t e = launch_gauss_legendre((int)n, a, b, nodes, weights, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  return e == cudaSuccess ? RCI_OK : RCI_ECUDA;
+}
+
+rci_status rci_get_eps(rci_grid* g, double* eps_out) {
+  if (!g) return RCI_EINVAL;
+  if (!eps_out) return fail(g, RCI_EINVAL, "eps_out is NULL");
+  if (!g->has_design) return fail(g, RCI_ESTATE, "no design set");
+  DeviceGuard dg(g->device);
+  CK(cudaMemcpyAsync(eps_out, g->eps, sizeof(double) * g->N, cudaMemcpyDeviceToDevice, g->s), "eps");
+  CK(cudaStreamSynchronize(g->s), "eps");
+  return RCI_OK;
+}
+
+rci_status rci_apply_operator(rci_grid* g, const double* x, double* y) {
+  if (!g) return RCI_EINVAL;
+  if (!x || !y) return fail(g, RCI_EINVAL, "NULL vector");
+  if (!g->has_design) return fail(g, RCI_ESTATE, "no design set");
+  DeviceGuard dg(g->device);
+  CK(launch_apply_A(g->g, g->dg, g->cx, g->cy, (const double2*)x, (double2*)y, 1, g->s), "apply A");
+  CK(cudaStreamSynchronize(g->s), "apply A");
+  return RCI_OK;
+}
+
+uint64_t rci_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+rci_status rci_profile_enable(rci_grid* g, int on) {
+  if (!g) return RCI_EINVAL;
+  DeviceGuard dg(g->device);
+  Profiler& p = g->prof;
+  if (on && !p.pool) {
+    const int cap = 1 << 14;
+    p.pool = new (std::nothrow) cudaEvent_t[cap];
+    p.recs = new (std::nothrow) Profiler::Rec[cap];
+    if (!p.pool || !p.recs) return fail(g, RCI_ENOMEM, "profiler allocation failed");
+    for (int i = 0; i < cap; ++i) CK(cudaEventCreate(&p.pool[i]), "profiler events");
+    p.cap = cap;
+  }
+  CK(cudaStreamSynchronize(g->s), "profiler");
+  p.reset();
+  p.on = on != 0;
+  bcr_set_profiler(g->bcr, p.on ? &p : nullptr);
+  return RCI_OK;
+}
+
+rci_status rci_profile_read(rci_grid* g, rci_profile* out) {
+  if (!g || !out) return RCI_EINVAL;
+  DeviceGuard dg(g->device);
+  CK(cudaStreamSynchronize(g->s), "profiler");
+  if (g->prof.on) g->prof.collect();
+  std::memset(out, 0, sizeof(*out));
+  for (int f = 0; f < PF_COUNT && f < RCI_PROFILE_FAMILIES; ++f) {
+    out->ms[f] = g->prof.ms[f];
+    out->flops[f] = g->prof.flops[f];
+    out->bytes[f] = g->prof.bytes[f];
+    out->launches[f] = g->prof.launches[f];
+  }
+  return RCI_OK;
+}
+
+}  // extern "C"

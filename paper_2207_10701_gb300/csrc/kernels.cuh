@@ -1,0 +1,73 @@
+// Host-side launchers of every kernel in the library (internal interface).
+#pragma once
+
+#include "common.cuh"
+
+// ------------------------------------------------------------------ geometry
+struct GridGeom {
+  int nx, ny, npml, n_src, j_src, j_p0, j_p1, n_cells, cell_px;
+  double h, k0, k_sub, eps_pillar, eps_sub, eps_air, sigma_max, width;
+  int pml_m;
+};
+
+// assemble.cu
+cudaError_t launch_raster_eps(const GridGeom& g, const double* widths_dev, double* eps,
+                              int32_t* status, cudaStream_t s);
+cudaError_t launch_assemble(const GridGeom& g, const double* eps, double2* dg, double2* cx,
+                            double2* cy, cudaStream_t s);
+cudaError_t launch_apply_A(const GridGeom& g, const double2* dg, const double2* cx,
+                           const double2* cy, const double2* x, double2* y, int nrhs,
+                           cudaStream_t s);
+// r = b - A x and per-RHS partial sums of |r|^2 and |b|^2 (nblk x nrhs each)
+int residual_blocks(const GridGeom& g);
+cudaError_t launch_residual(const GridGeom& g, const double2* dg, const double2* cx,
+                            const double2* cy, const double2* b, const double2* x, double2* r,
+                            int nrhs, double* part_r, double* part_b, cudaStream_t s);
+// sums the (nblk x nrhs) partials per column: out[q] = sqrt(sum r) / sqrt(sum b)
+cudaError_t launch_ratio_norms(const double* part_r, const double* part_b, int nblk, int nrhs,
+                               double* out, cudaStream_t s);
+// x64 += (double) d (elementwise, n complex), optionally writes the float copy of r
+cudaError_t launch_add_f32(double2* x, const float2* d, int64_t n, cudaStream_t s);
+cudaError_t launch_to_f32(const double2* a, float2* out, int64_t n, cudaStream_t s);
+cudaError_t launch_to_f64(const float2* a, double2* out, int64_t n, cudaStream_t s);
+cudaError_t launch_axpy64(double2* x, const double2* d, int64_t n, cudaStream_t s);
+cudaError_t launch_check_finite(const double2* a, int64_t n, int32_t* status, cudaStream_t s);
+
+// rhs.cu
+cudaError_t launch_gauss_legendre(int n, double a, double b, double* nodes, double* weights,
+                                  cudaStream_t s);
+// conj(w) on the monitor row (n_src entries) for PLANEWAVE / VIRTUAL_FOCUS
+cudaError_t launch_planewave_row(const GridGeom& g, double theta_out, double2* crow,
+                                 cudaStream_t s);
+cudaError_t launch_virtual_focus_row(const GridGeom& g, double x_f, int d_rows, double2* crow,
+                                     double* scratch /* >= 2*VF_ORDER + 6*VF_NODES doubles */, cudaStream_t s);
+constexpr int VF_PANELS = 256, VF_ORDER = 32, VF_NODES = VF_PANELS * VF_ORDER;
+// scatter a row vector into a zeroed full-grid vector: b[(npml+t)*ny + row] = crow[t] (conj if asked)
+cudaError_t launch_scatter_row(const GridGeom& g, const double2* crow, int row, double2* b,
+                               cudaStream_t s);
+// planewave sources for nq angles, [i][j][q] layout, into a zeroed buffer
+cudaError_t launch_sources(const GridGeom& g, const double* theta, int nq, int ldq, double2* B,
+                           cudaStream_t s);
+// amp_q = sum_t crow[t] u[(npml+t)*ny + row][q]   (crow = conj(w));  f_q = |amp_q|^2
+cudaError_t launch_project_row(const GridGeom& g, const double2* crow, int row,
+                               const double2* U, int nq, int ldq, double* f, cudaStream_t s);
+cudaError_t launch_project_point(const GridGeom& g, int i_f, int j_f, const double2* U, int nq,
+                                 int ldq, double* f, cudaStream_t s);
+// v_src[t] = conj(z[(npml+t)*ny + j_src])
+cudaError_t launch_gather_source_row(const GridGeom& g, const double2* z, double2* v,
+                                     cudaStream_t s);
+cudaError_t launch_conj(double2* a, int64_t n, cudaStream_t s);
+// light: rule (theta, weight*rho) for cone / annulus with nq points
+cudaError_t launch_light_rule(int kind, double c, double th1, double th2, int nq, double* theta,
+                              double* wrho, cudaStream_t s);
+// W lags (closed forms) m = 0..n-1
+cudaError_t launch_w_lags(int kind, double c, double th1, double th2, double k_s, double h,
+                          int64_t n, double* lags, cudaStream_t s);
+// weighted sum out = sum_q w_q f_q (single block, deterministic)
+cudaError_t launch_weighted_sum(const double* w, const double* f, int nq, double* out,
+                                cudaStream_t s);
+
+// qform.cu
+int64_t qform_num_partials(int64_t n);
+cudaError_t launch_qform(const double2* v, const double* lags, int64_t n, double* partials,
+                         double* out_dev, cudaStream_t s);

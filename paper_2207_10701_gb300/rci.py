@@ -1,0 +1,323 @@
+"""ctypes binding of include/rci.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librci.so")
+
+OBJ_POINT, OBJ_PLANEWAVE, OBJ_VIRTUAL_FOCUS, OBJ_USER_ROW = 0, 1, 2, 3
+LIGHT_CONE, LIGHT_ANNULUS, LIGHT_USER_LAGS = 0, 1, 2
+FP64, FP32_REFINE = 0, 1
+
+STATUS = {0: "RCI_OK", 1: "RCI_EINVAL", 2: "RCI_ENOMEM", 3: "RCI_ECUDA", 4: "RCI_ESTATE",
+          5: "RCI_ESINGULAR", 6: "RCI_ENOCONV", 7: "RCI_ENUMERIC", 8: "RCI_ETIMEOUT"}
+
+
+class GridDescC(C.Structure):
+    _fields_ = [("n_cells", C.c_int32), ("ny", C.c_int32), ("ppl", C.c_int32),
+                ("cell_px", C.c_int32), ("npml", C.c_int32), ("rows_sub", C.c_int32),
+                ("rows_pillar", C.c_int32), ("src_offset", C.c_int32),
+                ("eps_pillar", C.c_double), ("eps_sub", C.c_double), ("eps_air", C.c_double),
+                ("pml_R0", C.c_double), ("pml_m", C.c_int32), ("prec", C.c_int32),
+                ("device", C.c_int32), ("reserved", C.c_int32)]
+
+
+class ObjectiveC(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("monitor_row", C.c_int32), ("i_f", C.c_int32),
+                ("j_f", C.c_int32), ("theta_out", C.c_double), ("x_f", C.c_double),
+                ("d_rows", C.c_int32), ("reserved", C.c_int32),
+                ("w_row", C.POINTER(C.c_double))]
+
+
+class LightC(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("c", C.c_double),
+                ("th1", C.c_double), ("th2", C.c_double), ("lags", C.POINTER(C.c_double))]
+
+
+class InfoC(C.Structure):
+    _fields_ = [("refine_iters", C.c_int32), ("reserved", C.c_int32),
+                ("rel_residual", C.c_double), ("ms_factor", C.c_double),
+                ("ms_solve", C.c_double), ("ms_qform", C.c_double)]
+
+
+PROFILE_FAMILIES = ["level0", "invert", "gemm", "solve", "residual", "qform", "setup", "spare"]
+
+
+class ProfileC(C.Structure):
+    _fields_ = [("ms", C.c_double * 8), ("flops", C.c_double * 8), ("bytes", C.c_double * 8),
+                ("launches", C.c_int64 * 8)]
+
+
+@dataclasses.dataclass
+class Info:
+    refine_iters: int
+    rel_residual: float
+    ms_factor: float
+    ms_solve: float
+    ms_qform: float
+
+    @staticmethod
+    def of(c: InfoC) -> "Info":
+        return Info(c.refine_iters, c.rel_residual, c.ms_factor, c.ms_solve, c.ms_qform)
+
+
+class RciError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+EXPORTED = {
+    "rci_create_grid": (C.c_int, [C.POINTER(GridDescC), _P, C.POINTER(_P)]),
+    "rci_destroy_grid": (C.c_int, [_P]),
+    "rci_grid_query": (C.c_int, [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                 C.POINTER(C.c_int64), C.POINTER(C.c_size_t)]),
+    "rci_set_design": (C.c_int, [_P, _P, C.c_int64, C.c_int]),
+    "rci_factor": (C.c_int, [_P]),
+    "rci_solve": (C.c_int, [_P, _P, _P, C.c_int64, C.POINTER(InfoC)]),
+    "rci_solve_reciprocal": (C.c_int, [_P, C.POINTER(ObjectiveC), _P, _P, C.POINTER(InfoC)]),
+    "rci_avg_intensity": (C.c_int, [_P, C.POINTER(ObjectiveC), C.POINTER(LightC), _D,
+                                    C.POINTER(InfoC)]),
+    "rci_solve_angles": (C.c_int, [_P, C.POINTER(ObjectiveC), _D, _D, C.c_int64, _D, _D,
+                                   C.POINTER(InfoC)]),
+    "rci_avg_bruteforce": (C.c_int, [_P, C.POINTER(ObjectiveC), C.POINTER(LightC), C.c_int64,
+                                     _D, _D, C.POINTER(InfoC)]),
+    "rci_qform_toeplitz": (C.c_int, [_P, _P, C.c_int64, _D, _P]),
+    "rci_gauss_legendre": (C.c_int, [C.c_int64, C.c_double, C.c_double, _P, _P, _P]),
+    "rci_get_eps": (C.c_int, [_P, _P]),
+    "rci_apply_operator": (C.c_int, [_P, _P, _P]),
+    "rci_profile_enable": (C.c_int, [_P, C.c_int]),
+    "rci_profile_read": (C.c_int, [_P, C.POINTER(ProfileC)]),
+    "rci_kernel_launches": (C.c_uint64, []),
+    "rci_status_str": (C.c_char_p, [C.c_int]),
+    "rci_last_error": (C.c_char_p, [_P]),
+}
+
+_lib = None
+
+
+def lib(path: str = LIB_PATH):
+    """Load librci.so (once).  Raises if it has not been built: there is no fallback."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing; build it with "
+                               "`python -m paper_2207_10701_gb300.build`")
+        L = C.CDLL(path)
+        for name, (res, args) in EXPORTED.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _check(st: int, handle=None):
+    if st != 0:
+        msg = lib().rci_last_error(handle).decode() if handle else ""
+        if not msg:
+            msg = lib().rci_status_str(st).decode()
+        raise RciError(st, msg)
+
+
+def _dptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _hptr(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _desc(d, prec=None, device=0) -> GridDescC:
+    return GridDescC(d.n_cells, d.ny, d.ppl, d.cell_px, d.npml, d.rows_sub, d.rows_pillar,
+                     d.src_offset, d.eps_pillar, d.eps_sub, d.eps_air, d.pml_R0, d.pml_m,
+                     d.prec if prec is None else prec, device, 0)
+
+
+def _objective(o, keep):
+    w = None
+    if getattr(o, "kind", None) == OBJ_USER_ROW:
+        w = np.ascontiguousarray(np.asarray(o.w_row, dtype=np.complex128)).view(np.float64)
+        keep.append(w)
+    return ObjectiveC(o.kind, o.monitor_row, o.i_f, o.j_f, o.theta_out, o.x_f, o.d_rows, 0,
+                      _hptr(w) if w is not None else None)
+
+
+def _light(L, keep):
+    lags = None
+    if L.kind == LIGHT_USER_LAGS:
+        lags = np.ascontiguousarray(np.asarray(L.lags, dtype=np.float64))
+        keep.append(lags)
+    return LightC(L.kind, 0, L.c, L.th1, L.th2, _hptr(lags) if lags is not None else None)
+
+
+class Grid:
+    """One geometry on one CUDA device (owns the operator, the factorisation and the
+    work buffers).  ``desc`` is any object with the fields of rci_grid_desc."""
+
+    def __init__(self, desc, prec=None, device: int = 0, stream=None):
+        torch = _torch()
+        self.device = device
+        self.torch_device = torch.device("cuda", device)
+        self._stream = _stream(stream)
+        h = C.c_void_p()
+        _check(lib().rci_create_grid(C.byref(_desc(desc, prec, device)), self._stream, C.byref(h)))
+        self._h = h
+        nx, ny, ns, by = C.c_int64(), C.c_int64(), C.c_int64(), C.c_size_t()
+        _check(lib().rci_grid_query(h, C.byref(nx), C.byref(ny), C.byref(ns), C.byref(by)), h)
+        self.nx, self.ny, self.n_src = nx.value, ny.value, ns.value
+        self.N = self.nx * self.ny
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rci_destroy_grid(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def profile(self, on: bool = True):
+        """Start (reset) or stop bracketing kernel families with CUDA events."""
+        _check(lib().rci_profile_enable(self._h, 1 if on else 0), self._h)
+
+    def profile_read(self) -> dict:
+        """{family: {"ms", "flops", "bytes", "launches"}} accumulated since profile(True)."""
+        p = ProfileC()
+        _check(lib().rci_profile_read(self._h, C.byref(p)), self._h)
+        return {f: {"ms": p.ms[i], "flops": p.flops[i], "bytes": p.bytes[i],
+                    "launches": p.launches[i]} for i, f in enumerate(PROFILE_FAMILIES[:7])}
+
+    def device_bytes(self) -> int:
+        by = C.c_size_t()
+        _check(lib().rci_grid_query(self._h, None, None, None, C.byref(by)), self._h)
+        return by.value
+
+    def set_design(self, widths):
+        torch = _torch()
+        if isinstance(widths, torch.Tensor) and widths.is_cuda:
+            w = widths.to(torch.float64).contiguous()
+            _check(lib().rci_set_design(self._h, _dptr(w), w.numel(), 1), self._h)
+        else:
+            w = np.ascontiguousarray(np.asarray(widths, dtype=np.float64))
+            _check(lib().rci_set_design(self._h, w.ctypes.data_as(_P), w.size, 0), self._h)
+
+    def factor(self):
+        _check(lib().rci_factor(self._h), self._h)
+
+    def solve(self, b, nrhs: int = 1):
+        """b: complex128 CUDA tensor of nx*ny*nrhs entries ([i][j][q]); returns x."""
+        torch = _torch()
+        b = b.to(torch.complex128).contiguous()
+        x = torch.empty_like(b)
+        info = InfoC()
+        _check(lib().rci_solve(self._h, _dptr(b), _dptr(x), nrhs, C.byref(info)), self._h)
+        return x, Info.of(info)
+
+    def solve_reciprocal(self, obj, full: bool = False):
+        torch = _torch()
+        keep = []
+        oc = _objective(obj, keep)
+        v = torch.empty(self.n_src, dtype=torch.complex128, device=self.torch_device)
+        vf = torch.empty(self.N, dtype=torch.complex128, device=self.torch_device) if full else None
+        info = InfoC()
+        _check(lib().rci_solve_reciprocal(self._h, C.byref(oc), _dptr(v),
+                                          _dptr(vf) if full else None, C.byref(info)), self._h)
+        return (v, vf, Info.of(info)) if full else (v, Info.of(info))
+
+    def avg_intensity(self, obj, light):
+        keep = []
+        oc, lc = _objective(obj, keep), _light(light, keep)
+        out = C.c_double()
+        info = InfoC()
+        _check(lib().rci_avg_intensity(self._h, C.byref(oc), C.byref(lc), C.byref(out),
+                                       C.byref(info)), self._h)
+        return out.value, Info.of(info)
+
+    def solve_angles(self, obj, theta, weight):
+        keep = []
+        oc = _objective(obj, keep)
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+        wq = np.ascontiguousarray(np.asarray(weight, dtype=np.float64))
+        f = np.empty(th.size)
+        avg = C.c_double()
+        info = InfoC()
+        _check(lib().rci_solve_angles(self._h, C.byref(oc), _hptr(th), _hptr(wq), th.size,
+                                      _hptr(f), C.byref(avg), C.byref(info)), self._h)
+        return avg.value, f, Info.of(info)
+
+    def avg_bruteforce(self, obj, light, nq: int):
+        keep = []
+        oc, lc = _objective(obj, keep), _light(light, keep)
+        f = np.empty(nq)
+        avg = C.c_double()
+        info = InfoC()
+        _check(lib().rci_avg_bruteforce(self._h, C.byref(oc), C.byref(lc), nq, _hptr(f),
+                                        C.byref(avg), C.byref(info)), self._h)
+        return avg.value, f, Info.of(info)
+
+    def eps(self):
+        torch = _torch()
+        e = torch.empty(self.N, dtype=torch.float64, device=self.torch_device)
+        _check(lib().rci_get_eps(self._h, _dptr(e)), self._h)
+        return e.view(self.nx, self.ny)
+
+    def apply_operator(self, x):
+        torch = _torch()
+        x = x.to(torch.complex128).contiguous()
+        y = torch.empty_like(x)
+        _check(lib().rci_apply_operator(self._h, _dptr(x), _dptr(y)), self._h)
+        return y
+
+
+def kernel_launches() -> int:
+    """Kernels launched by librci in this process so far."""
+    return int(lib().rci_kernel_launches())
+
+
+def qform_toeplitz(v, lags, stream=None) -> float:
+    """sum_{i,l} conj(v_i) lags[|i-l|] v_l on the device (v complex128, lags float64, CUDA)."""
+    torch = _torch()
+    v = v.to(torch.complex128).contiguous()
+    lags = lags.to(torch.float64).contiguous()
+    out = C.c_double()
+    _check(lib().rci_qform_toeplitz(_dptr(v), _dptr(lags), v.numel(), C.byref(out),
+                                    _stream(stream)))
+    return out.value
+
+
+def gauss_legendre(n: int, a: float = -1.0, b: float = 1.0, device: int = 0, stream=None):
+    torch = _torch()
+    x = torch.empty(n, dtype=torch.float64, device=torch.device("cuda", device))
+    w = torch.empty_like(x)
+    _check(lib().rci_gauss_legendre(n, a, b, _dptr(x), _dptr(w), _stream(stream)))
+    return x, w

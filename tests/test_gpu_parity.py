@@ -1,0 +1,273 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 CPU oracle.
+
+Tolerances (relative): FP64 grids 1e-9 on the averaged figure of merit F, FP32 grids
+with FP64 refinement 1e-8 (the stated targets); fields compared element by element
+against the largest entry at 1e-9 / 1e-8; the permittivity raster bit for bit; the
+FP64 stencil at 1e-14; the FP64 quadratic form at 1e-12."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.grid import Grid as OGrid, rasterize_eps, stencil_coefficients, apply_A
+from oracle.light import W_lags, gauss_legendre as o_gl, quadrature_rule
+from oracle.reciprocal import Evaluation, qform_direct
+from oracle.solve import Solver
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2207_10701_gb300 as P  # noqa: E402
+
+TOL_F = {P.FP64: 1e-9, P.FP32_REFINE: 1e-8}
+
+
+def _cplx(t):
+    return t.detach().cpu().numpy()
+
+
+def _widths(wl, seed):
+    period = wl.grid.cell_px / wl.grid.ppl
+    return W.widths(wl.grid.n_cells, seed, lo=0.2 * period, hi=min(0.36, 0.9 * period))
+
+
+def _grid(wl, prec, seed=0):
+    g = P.Grid(wl.grid, prec=prec)
+    ws = _widths(wl, seed)
+    g.set_design(ws)
+    return g, ws
+
+
+CASES = {
+    "tiny_point": lambda: W.tiny(kind=W.OBJ_POINT),
+    "tiny_plane": lambda: W.tiny(kind=W.OBJ_PLANEWAVE),
+    "tiny_virtual": lambda: W.tiny(kind=W.OBJ_VIRTUAL_FOCUS),
+    "small_plane": lambda: W.small(kind=W.OBJ_PLANEWAVE),
+    "small_point": lambda: W.small(kind=W.OBJ_POINT),
+    "small_virtual": lambda: W.small(kind=W.OBJ_VIRTUAL_FOCUS),
+    "ragged": lambda: W.Workload("ragged", W.GridDesc(n_cells=7, ny=50, cell_px=5, npml=9,
+                                                      rows_sub=7, rows_pillar=9),
+                                 W.Objective(kind=W.OBJ_PLANEWAVE, monitor_row=30, theta_out=0.1),
+                                 W.Light(W.LIGHT_CONE, c=0.3), 40),
+    "one_cell": lambda: W.Workload("one_cell", W.GridDesc(n_cells=1, ny=40, npml=6, rows_sub=5,
+                                                          rows_pillar=6),
+                                   W.Objective(kind=W.OBJ_POINT, i_f=10, j_f=25),
+                                   W.Light(W.LIGHT_ANNULUS, th1=0.1, th2=0.4), 20),
+}
+
+
+@pytest.mark.parametrize("name", ["tiny_point", "small_plane", "ragged", "one_cell"])
+def test_raster_bit_exact(name):
+    wl = CASES[name]()
+    g, ws = _grid(wl, P.FP64, seed=3)
+    og = OGrid(wl.grid)
+    ref = rasterize_eps(og, ws)
+    got = g.eps().cpu().numpy()
+    assert np.array_equal(got, ref)
+
+
+def test_raster_bit_exact_c2():
+    wl = W.c2_collimator()
+    g, ws = _grid(wl, P.FP64, seed=11)
+    assert np.array_equal(g.eps().cpu().numpy(), rasterize_eps(OGrid(wl.grid), ws))
+
+
+@pytest.mark.parametrize("name", ["tiny_point", "small_plane", "ragged"])
+def test_stencil_matches_oracle(name):
+    wl = CASES[name]()
+    g, ws = _grid(wl, P.FP64)
+    og = OGrid(wl.grid)
+    coeffs = stencil_coefficients(og, rasterize_eps(og, ws))
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((og.nx, og.ny)) + 1j * rng.standard_normal((og.nx, og.ny))
+    ref = apply_A(og, coeffs, x)
+    got = _cplx(g.apply_operator(torch.from_numpy(x.ravel()).cuda())).reshape(og.nx, og.ny)
+    assert np.max(np.abs(got - ref)) <= 1e-14 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("prec", [P.FP64, P.FP32_REFINE])
+@pytest.mark.parametrize("name", ["tiny_point", "small_plane", "ragged", "one_cell"])
+def test_solve_matches_oracle(name, prec):
+    wl = CASES[name]()
+    g, ws = _grid(wl, prec)
+    g.factor()
+    og = OGrid(wl.grid)
+    s = Solver(og, rasterize_eps(og, ws))
+    rng = np.random.default_rng(2)
+    b = rng.standard_normal((og.nx, og.ny)) + 1j * rng.standard_normal((og.nx, og.ny))
+    ref = s.solve(b)
+    x, info = g.solve(torch.from_numpy(b.ravel()).cuda())
+    got = _cplx(x).reshape(og.nx, og.ny)
+    assert np.max(np.abs(got - ref)) <= TOL_F[prec] * np.max(np.abs(ref)), info
+
+
+@pytest.mark.parametrize("prec", [P.FP64, P.FP32_REFINE])
+def test_multi_rhs_solve_matches_single(prec):
+    wl = CASES["small_plane"]()
+    g, ws = _grid(wl, prec)
+    g.factor()
+    og = OGrid(wl.grid)
+    s = Solver(og, rasterize_eps(og, ws))
+    rng = np.random.default_rng(4)
+    nq = 5
+    b = rng.standard_normal((og.nx, og.ny, nq)) + 1j * rng.standard_normal((og.nx, og.ny, nq))
+    ref = s.solve(b)
+    x, _ = g.solve(torch.from_numpy(b.ravel()).cuda(), nrhs=nq)
+    got = _cplx(x).reshape(og.nx, og.ny, nq)
+    for q in range(nq):
+        assert np.max(np.abs(got[..., q] - ref[..., q])) <= TOL_F[prec] * np.max(np.abs(ref[..., q]))
+
+
+@pytest.mark.parametrize("prec", [P.FP64, P.FP32_REFINE])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_avg_intensity_matches_oracle(name, prec):
+    wl = CASES[name]()
+    g, ws = _grid(wl, prec, seed=5)
+    g.factor()
+    ev = Evaluation(wl, ws)
+    F_ref, v_ref = ev.reciprocal()
+    F, info = g.avg_intensity(wl.objective, wl.light)
+    assert abs(F - F_ref) <= TOL_F[prec] * abs(F_ref), (F, F_ref, info)
+    v, _ = g.solve_reciprocal(wl.objective)
+    v = _cplx(v)
+    assert np.max(np.abs(v - v_ref)) <= TOL_F[prec] * np.max(np.abs(v_ref))
+
+
+@pytest.mark.parametrize("prec", [P.FP64, P.FP32_REFINE])
+def test_avg_intensity_c1(prec):
+    wl = W.c1_concentrator()
+    g, ws = _grid(wl, prec, seed=0)
+    g.factor()
+    F_ref, v_ref = Evaluation(wl, ws).reciprocal()
+    F, info = g.avg_intensity(wl.objective, wl.light)
+    assert abs(F - F_ref) <= TOL_F[prec] * F_ref, (F, F_ref, info)
+
+
+@pytest.mark.parametrize("prec", [P.FP32_REFINE, P.FP64])
+def test_avg_intensity_c2_full_size(prec):
+    # the bench workload at full size (oracle: ~10 s of CPU)
+    wl = W.c2_collimator()
+    g, ws = _grid(wl, prec, seed=0)
+    g.factor()
+    F_ref, v_ref = Evaluation(wl, ws).reciprocal()
+    F, info = g.avg_intensity(wl.objective, wl.light)
+    assert abs(F - F_ref) <= TOL_F[prec] * F_ref, (F, F_ref, info)
+    v, _ = g.solve_reciprocal(wl.objective)
+    idx = np.random.default_rng(0).choice(v.numel(), 64, replace=False)
+    vs = _cplx(v)[idx]
+    assert np.max(np.abs(vs - v_ref[idx])) <= TOL_F[prec] * np.max(np.abs(v_ref))
+
+
+def test_user_lags_and_user_row_objective():
+    wl = CASES["small_plane"]()
+    g, ws = _grid(wl, P.FP64, seed=9)
+    g.factor()
+    og = OGrid(wl.grid)
+    rng = np.random.default_rng(3)
+    row = rng.standard_normal(og.n_src) + 1j * rng.standard_normal(og.n_src)
+    obj = W.Objective(kind=W.OBJ_USER_ROW, monitor_row=wl.objective.monitor_row, w_row=row)
+    # the paper's printed cone formula (no Jacobian, theta for sin theta) as user lags
+    c = 0.3
+    lags = np.sinc(og.h * np.arange(og.n_src) * 2 * np.pi * np.sin(c) / np.pi)
+    light = W.Light(W.LIGHT_USER_LAGS, lags=lags)
+    wl2 = W.Workload("u", wl.grid, obj, light, 0)
+    F_ref, _ = Evaluation(wl2, ws).reciprocal()
+    F, _ = g.avg_intensity(obj, light)
+    assert abs(F - F_ref) <= 1e-9 * abs(F_ref)
+
+
+@pytest.mark.parametrize("n", [1, 5, 127, 128, 129, 1000, 4000])
+def test_qform_matches_oracle(n):
+    rng = np.random.default_rng(n)
+    v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    light = W.Light(W.LIGHT_ANNULUS, th1=0.17, th2=0.52)
+    lags = W_lags(light, 2 * math.pi * math.sqrt(2.1), 0.05, n)
+    ref = qform_direct(v, lags)
+    got = P.qform_toeplitz(torch.from_numpy(v).cuda(), torch.from_numpy(lags).cuda())
+    assert abs(got - ref) <= 1e-12 * abs(ref)
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 32, 201, 500])
+def test_gauss_legendre_matches_oracle(n):
+    x, w = P.gauss_legendre(n, -0.3, 0.7)
+    xr, wr = o_gl(n)
+    assert np.max(np.abs(x.cpu().numpy() - (0.5 * xr + 0.2))) < 1e-14
+    assert np.max(np.abs(w.cpu().numpy() - 0.5 * wr)) < 1e-14
+
+
+@pytest.mark.parametrize("prec", [P.FP64, P.FP32_REFINE])
+@pytest.mark.parametrize("name", ["tiny_point", "small_plane", "small_virtual", "one_cell"])
+def test_bruteforce_matches_oracle(name, prec):
+    wl = CASES[name]()
+    g, ws = _grid(wl, prec, seed=6)
+    g.factor()
+    ev = Evaluation(wl, ws)
+    nq = 24
+    Fb_ref, th, wq, f_ref = ev.bruteforce(nq)
+    Fb, f, _ = g.avg_bruteforce(wl.objective, wl.light, nq)
+    assert np.max(np.abs(f - f_ref)) <= TOL_F[prec] * np.max(f_ref)
+    assert abs(Fb - Fb_ref) <= TOL_F[prec] * Fb_ref
+    Fa, fa, _ = g.solve_angles(wl.objective, th, wq)
+    assert abs(Fa - Fb_ref) <= TOL_F[prec] * Fb_ref
+
+
+def test_bruteforce_c1_201_angles_equals_reciprocal():
+    wl = W.c1_concentrator()
+    g, ws = _grid(wl, P.FP32_REFINE)
+    g.factor()
+    F, _ = g.avg_intensity(wl.objective, wl.light)
+    Fb, f, _ = g.avg_bruteforce(wl.objective, wl.light, 201)
+    assert abs(Fb - F) <= 1e-8 * F
+    F_ref, _ = Evaluation(wl, ws).reciprocal()
+    assert abs(Fb - F_ref) <= 1e-8 * F_ref
+
+
+def test_errors_are_reported():
+    wl = CASES["tiny_point"]()
+    g = P.Grid(wl.grid, prec=P.FP64)
+    with pytest.raises(P.RciError) as e:
+        g.factor()
+    assert e.value.status == 4                        # RCI_ESTATE before a design
+    with pytest.raises(P.RciError) as e:
+        g.set_design(np.full(wl.grid.n_cells, 0.5))   # wider than the period
+    assert e.value.status == 1
+    g.set_design(W.widths(wl.grid.n_cells, 0))
+    with pytest.raises(P.RciError) as e:
+        g.avg_intensity(wl.objective, wl.light)       # not factored
+    assert e.value.status == 4
+    g.factor()
+    bad = W.Objective(kind=W.OBJ_POINT, i_f=10_000, j_f=0)
+    with pytest.raises(P.RciError) as e:
+        g.avg_intensity(bad, wl.light)
+    assert e.value.status == 1
+    with pytest.raises(P.RciError) as e:
+        g.avg_intensity(wl.objective, W.Light(W.LIGHT_CONE, c=2.0))
+    assert e.value.status == 1
+    bad_dev = torch.tensor(W.widths(wl.grid.n_cells, 1), dtype=torch.float64, device="cuda")
+    bad_dev[1] = 0.45
+    g.set_design(bad_dev)                             # device widths: checked on the device
+    with pytest.raises(P.RciError) as e:
+        g.factor()
+    assert e.value.status == 1
+    g.set_design(W.widths(wl.grid.n_cells, 0))
+    g.factor()
+    b = torch.zeros(g.N, dtype=torch.complex128, device="cuda")
+    b[3] = float("nan")
+    with pytest.raises(P.RciError) as e:
+        g.solve(b)
+    assert e.value.status == 7                        # RCI_ENUMERIC
+
+
+def test_repeat_is_bitwise_deterministic():
+    wl = CASES["small_plane"]()
+    g, ws = _grid(wl, P.FP32_REFINE)
+    g.factor()
+    F1, _ = g.avg_intensity(wl.objective, wl.light)
+    g.set_design(ws)
+    g.factor()
+    F2, _ = g.avg_intensity(wl.objective, wl.light)
+    assert F1 == F2
