@@ -199,6 +199,25 @@ rci_status rci_avg_bruteforce(rci_grid* g, const rci_objective* obj, const rci_l
 rci_status rci_qform_toeplitz(const double* v, const double* lags, int64_t n, double* out,
                               void* stream);
 
+/* Allocation-free variant of rci_qform_toeplitz (the paper has no counterpart; this is
+ * a library service).  rci_qform_toeplitz allocates its scratch with cudaMalloc and
+ * releases it with cudaFree, and cudaFree synchronises the whole device.  Callers that
+ * hand all device memory to their own pool, or that keep several streams busy and must
+ * not be stalled by a device-wide synchronisation, call this one instead: it allocates
+ * nothing, does not synchronise, and writes the result to device memory in stream order.
+ *   out = sum_{i,l < n} conj(v_i) lags[|i - l|] v_l
+ * v: DEVICE complex128[n]; lags: DEVICE float64[n]; out: DEVICE double[1];
+ * stream: cudaStream_t or NULL.  1 <= n <= RCI_QFORM_NOALLOC_MAX_N, else RCI_EINVAL.
+ * Scratch: a fixed device array of 32896 doubles (257 KB) inside the library, held by
+ * every device that loads the library until the process exits and shared by all calls
+ * on that device: calls that overlap on the GPU (e.g. on two streams) race.  Each call
+ * overwrites all the scratch it reads, so nothing needs clearing between calls.  The
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture. */
+#define RCI_QFORM_NOALLOC_MAX_N 32768
+rci_status rci_qform_toeplitz_noalloc(const double* v, const double* lags, int64_t n,
+                                      double* out, void* stream);
+
 /* n-point Gauss-Legendre rule on [a, b] computed on the device (Newton on the
  * three-term recurrence).  nodes, weights: DEVICE float64[n], ascending nodes. */
 rci_status rci_gauss_legendre(int64_t n, double a, double b, double* nodes, double* weights,

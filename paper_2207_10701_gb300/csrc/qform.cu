@@ -5,6 +5,8 @@
 // and the Toeplitz matrix symmetric).  Per pair two FP64 FMAs: the block accumulates
 // s_i = sum_l W_{|i-l|} v_l, then adds Re(conj(v_i) s_i).  Per-tile partials are summed
 // in a fixed order by a second kernel, so the result is bitwise reproducible.
+#include <mutex>
+
 #include "kernels.cuh"
 
 namespace {
@@ -90,4 +92,60 @@ cudaError_t launch_qform(const double2* v, const double* lags, int64_t n, double
   RCI_CUDA_TRY(cudaGetLastError());
   sum_partials_kernel<<<1, 256, 0, s>>>(partials, np, out_dev); rci_note_launch();
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- allocation-free variant
+// rci_qform_toeplitz allocates its per-tile partials with cudaMalloc and releases them
+// with cudaFree, which synchronises the whole device.  Callers that own all device
+// memory through their own pool, or that overlap work on several streams and must not
+// be stalled by a device-wide synchronisation, use rci_qform_toeplitz_noalloc instead:
+// its partials live in the file-scope array below, which every device that loads this
+// library holds until the process exits.
+//
+// The array is shared by every call on a device.  Each call writes every partial it
+// later reads and then the result, so nothing has to start at zero and stale contents
+// of an earlier (larger) call are never read; two calls that overlap on the GPU (for
+// example on two streams) race on the array.
+namespace {
+constexpr int64_t NOALLOC_TILES = RCI_QFORM_NOALLOC_MAX_N / QT;                // 256
+constexpr int64_t NOALLOC_PARTIALS = NOALLOC_TILES * (NOALLOC_TILES + 1) / 2;  // 32896
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static_assert(RCI_QFORM_NOALLOC_MAX_N % QT == 0, "maximum size must be a whole number of tiles");
+}  // namespace
+
+static __device__ __align__(256) double g_qform_noalloc_scratch[NOALLOC_PARTIALS];
+
+namespace {
+std::once_flag g_noalloc_once[NOALLOC_MAX_DEVICES];
+cudaError_t g_noalloc_err[NOALLOC_MAX_DEVICES];
+double* g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+
+// Device address of the scratch array on the current device.  In host code the array's
+// name is only a host-side stand-in, so the address is looked up once per device (with
+// that device current) and cached.
+cudaError_t noalloc_scratch(double** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::call_once(g_noalloc_once[dev], [dev]() {
+    void* p = nullptr;
+    g_noalloc_err[dev] = cudaGetSymbolAddress(&p, g_qform_noalloc_scratch);
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  });
+  if (g_noalloc_err[dev] != cudaSuccess) return g_noalloc_err[dev];
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" rci_status rci_qform_toeplitz_noalloc(const double* v, const double* lags, int64_t n,
+                                                 double* out, void* stream) {
+  if (!v || !lags || !out || n < 1) return RCI_EINVAL;
+  if (n > RCI_QFORM_NOALLOC_MAX_N) return RCI_EINVAL;
+  double* scratch = nullptr;
+  if (noalloc_scratch(&scratch) != cudaSuccess) return RCI_ECUDA;
+  if (launch_qform((const double2*)v, lags, n, scratch, out, (cudaStream_t)stream) != cudaSuccess)
+    return RCI_ECUDA;
+  return RCI_OK;
 }

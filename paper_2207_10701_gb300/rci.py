@@ -90,6 +90,7 @@ EXPORTED = {
     "rci_avg_bruteforce": (C.c_int, [_P, C.POINTER(ObjectiveC), C.POINTER(LightC), C.c_int64,
                                      _D, _D, C.POINTER(InfoC)]),
     "rci_qform_toeplitz": (C.c_int, [_P, _P, C.c_int64, _D, _P]),
+    "rci_qform_toeplitz_noalloc": (C.c_int, [_P, _P, C.c_int64, _P, _P]),
     "rci_gauss_legendre": (C.c_int, [C.c_int64, C.c_double, C.c_double, _P, _P, _P]),
     "rci_get_eps": (C.c_int, [_P, _P]),
     "rci_apply_operator": (C.c_int, [_P, _P, _P]),
@@ -313,6 +314,23 @@ def qform_toeplitz(v, lags, stream=None) -> float:
     _check(lib().rci_qform_toeplitz(_dptr(v), _dptr(lags), v.numel(), C.byref(out),
                                     _stream(stream)))
     return out.value
+
+
+QFORM_NOALLOC_MAX_N = 32768
+
+
+def qform_toeplitz_noalloc(v, lags, out, stream=None):
+    """Allocation-free form of qform_toeplitz for callers that must not allocate device
+    memory: the result goes to the CUDA float64 tensor ``out`` (one element) in stream
+    order, without synchronising.  n <= QFORM_NOALLOC_MAX_N."""
+    torch = _torch()
+    if v.dtype != torch.complex128 or lags.dtype != torch.float64 or out.dtype != torch.float64:
+        raise TypeError("v complex128, lags and out float64")
+    if not (v.is_contiguous() and lags.is_contiguous()):
+        raise ValueError("contiguous tensors required")
+    _check(lib().rci_qform_toeplitz_noalloc(_dptr(v), _dptr(lags), v.numel(), _dptr(out),
+                                            _stream(stream)))
+    return out
 
 
 def gauss_legendre(n: int, a: float = -1.0, b: float = 1.0, device: int = 0, stream=None):
