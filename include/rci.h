@@ -155,6 +155,13 @@ rci_status rci_factor(rci_grid* g);
  * FP64 grids take up to two refinement steps.  info (HOST, may be NULL). */
 rci_status rci_solve(rci_grid* g, const double* b, double* x, int64_t nrhs, rci_info* info);
 
+/* Iterative refinement settings of the grid: stop when ||b - A x||_2 / ||b||_2 <= tol
+ * (FP64 stencil residual) or after max_steps corrections (the first FP32 solve is not
+ * counted).  Defaults: FP32_REFINE tol 1e-10, 12 steps; FP64 tol 1e-13, 2 steps.  A
+ * solve that ends above tol returns RCI_ENOCONV with its best value (FP64 grids only
+ * report ENOCONV above 1e-9).  tol > 0, 0 <= max_steps <= 100. */
+rci_status rci_set_refinement(rci_grid* g, double tol, int32_t max_steps);
+
 /* Reciprocal solve of Eq. 7: v = A^{-dag} w = conj(A^{-1} conj(w)) (A symmetric).
  * v_src_out: DEVICE complex128[n_src], v on the source row j_src over S, or NULL.
  * v_full_out: DEVICE complex128[nx*ny], v on the whole grid, or NULL.

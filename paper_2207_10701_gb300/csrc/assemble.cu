@@ -39,7 +39,9 @@ __device__ __forceinline__ double2 sy_at(const GridGeom& g, int j, bool half) {
 // Widths outside (0, period) are flagged in *status (DEV_BADINPUT); every width is
 // seen by the columns of its own cell.
 __global__ void raster_kernel(GridGeom g, const double* __restrict__ widths,
-                              double* __restrict__ eps, int32_t* status) {
+                              double* __restrict__ eps, const double2* __restrict__ dg0,
+                              const double2* __restrict__ kss, double2* __restrict__ dg,
+                              int32_t* status) {
   int i = blockIdx.y;
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.nx || j >= g.ny) return;
@@ -70,11 +72,19 @@ __global__ void raster_kernel(GridGeom g, const double* __restrict__ widths,
     double f = acc / g.h;
     v = __dadd_rn(g.eps_air, __dmul_rn(f, __dsub_rn(g.eps_pillar, g.eps_air)));
   }
-  eps[(int64_t)i * g.ny + j] = v;
+  int64_t k = (int64_t)i * g.ny + j;
+  eps[k] = v;
+  // the only permittivity-dependent coefficient: dg = dg0 + k0^2 eps s_x s_y
+  double2 ks = kss[k];
+  double2 d0 = dg0[k];
+  dg[k] = mkc(fma(v, ks.x, d0.x), fma(v, ks.y, d0.y));
 }
 
-__global__ void assemble_kernel(GridGeom g, const double* __restrict__ eps, double2* __restrict__ dg,
-                                double2* __restrict__ cx, double2* __restrict__ cy) {
+// Design-independent part of the stencil, computed once per grid:
+//   dg0 = -s_y/h^2 (1/s_x^{i+1/2} + 1/s_x^{i-1/2}) - s_x/h^2 (1/s_y^{j+1/2} + 1/s_y^{j-1/2}),
+//   kss = k0^2 s_x^i s_y^j,  cx, cy the couplings.
+__global__ void pml_coeff_kernel(GridGeom g, double2* __restrict__ dg0, double2* __restrict__ kss,
+                                 double2* __restrict__ cx, double2* __restrict__ cy) {
   int i = blockIdx.y;
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.nx || j >= g.ny) return;
@@ -83,10 +93,9 @@ __global__ void assemble_kernel(GridGeom g, const double* __restrict__ eps, doub
   double2 isxm = crecip(sx_at(g, i, true)), isxp = crecip(sx_at(g, i + 1, true));
   double2 isym = crecip(sy_at(g, j, true)), isyp = crecip(sy_at(g, j + 1, true));
   double2 SYh = (1.0 / h2) * sy, SXh = (1.0 / h2) * sx;
-  double2 d = -(SYh * (isxp + isxm)) - SXh * (isyp + isym) +
-              (g.k0 * g.k0 * eps[(int64_t)i * g.ny + j]) * (sx * sy);
   int64_t k = (int64_t)i * g.ny + j;
-  dg[k] = d;
+  dg0[k] = -(SYh * (isxp + isxm)) - SXh * (isyp + isym);
+  kss[k] = (g.k0 * g.k0) * (sx * sy);
   if (i < g.nx - 1) cx[k] = SYh * isxp;
   cy[k] = (j < g.ny - 1) ? SXh * isyp : mkc(0.0, 0.0);
 }
@@ -111,11 +120,58 @@ __global__ void apply_A_kernel(GridGeom g, const double2* __restrict__ dg,
 constexpr int RES_THREADS = 256;
 constexpr int RES_BLOCKS = 1216;  // 8 blocks on each of the 152 SMs (grid-stride loop)
 
-// r = b - A x, and per-block partials of |r|^2 and |b|^2 for each right-hand side
-// (grid-stride over unknowns; one partial per (block, q)).  The partials are gathered
-// with shared-memory atomics, so the norms (used for the stopping test and the
-// reported residual) may differ in the last bits between runs; r itself is exact
-// to the order of the stencil sum.
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// Single right-hand side: r = b - A x and per-block partial sums of |r|^2, |b|^2, reduced
+// in a fixed order (warp shuffles, then warps in order), so the norms are reproducible.
+__global__ void __launch_bounds__(RES_THREADS)
+residual1_kernel(GridGeom g, const double2* __restrict__ dg, const double2* __restrict__ cx,
+                 const double2* __restrict__ cy, const double2* __restrict__ b,
+                 const double2* __restrict__ x, double2* __restrict__ r,
+                 double* __restrict__ part_r, double* __restrict__ part_b) {
+  __shared__ double wr[RES_THREADS / 32], wb[RES_THREADS / 32];
+  const int N = g.nx * g.ny;
+  double sr = 0.0, sb = 0.0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    int i = k / g.ny, j = k - i * g.ny;
+    double2 acc = dg[k] * x[k];
+    if (i > 0) acc = cfma(cx[k - g.ny], x[k - g.ny], acc);
+    if (i < g.nx - 1) acc = cfma(cx[k], x[k + g.ny], acc);
+    if (j > 0) acc = cfma(cy[k - 1], x[k - 1], acc);
+    if (j < g.ny - 1) acc = cfma(cy[k], x[k + 1], acc);
+    double2 bb = b[k];
+    double2 rr = bb - acc;
+    r[k] = rr;
+    sr = fma(rr.x, rr.x, fma(rr.y, rr.y, sr));
+    sb = fma(bb.x, bb.x, fma(bb.y, bb.y, sb));
+  }
+  sr = warp_sum_d(sr);
+  sb = warp_sum_d(sb);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    wr[warp] = sr;
+    wb[warp] = sb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, c = 0.0;
+    for (int w = 0; w < RES_THREADS / 32; ++w) {
+      a += wr[w];
+      c += wb[w];
+    }
+    part_r[blockIdx.x] = a;
+    part_b[blockIdx.x] = c;
+  }
+}
+
+// Several right-hand sides: r = b - A x, and per-block partials of |r|^2 and |b|^2 for
+// each right-hand side (grid-stride over unknowns; one partial per (block, q)).  The
+// partials are gathered with shared-memory atomics, so these norms (used for the
+// stopping test and the reported residual) may differ in the last bits between runs;
+// r itself is exact to the order of the stencil sum.
 __global__ void __launch_bounds__(RES_THREADS)
 residual_kernel(GridGeom g, const double2* __restrict__ dg, const double2* __restrict__ cx,
                 const double2* __restrict__ cy, const double2* __restrict__ b,
@@ -157,17 +213,29 @@ residual_kernel(GridGeom g, const double2* __restrict__ dg, const double2* __res
   }
 }
 
-__global__ void ratio_norms_kernel(const double* __restrict__ part_r,
-                                   const double* __restrict__ part_b, int nblk, int nrhs,
-                                   double* __restrict__ out) {
-  int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nrhs) return;
-  double sr = 0.0, sb = 0.0;
-  for (int b = 0; b < nblk; ++b) {
-    sr += part_r[(int64_t)b * nrhs + q];
-    sb += part_b[(int64_t)b * nrhs + q];
+// out[q] = sqrt(sum_b part_r[b][q]) / sqrt(sum_b part_b[b][q]); one block per q, fixed-order
+// strided sums then a tree.
+__global__ void __launch_bounds__(256)
+ratio_norms_kernel(const double* __restrict__ part_r, const double* __restrict__ part_b, int nblk,
+                   int nrhs, double* __restrict__ out) {
+  __shared__ double sr[256], sb[256];
+  const int q = blockIdx.x;
+  double a = 0.0, c = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+    a += part_r[(int64_t)b * nrhs + q];
+    c += part_b[(int64_t)b * nrhs + q];
   }
-  out[q] = sb > 0.0 ? sqrt(sr) / sqrt(sb) : sqrt(sr);
+  sr[threadIdx.x] = a;
+  sb[threadIdx.x] = c;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sr[threadIdx.x] += sr[threadIdx.x + s];
+      sb[threadIdx.x] += sb[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[q] = sb[0] > 0.0 ? sqrt(sr[0]) / sqrt(sb[0]) : sqrt(sr[0]);
 }
 
 __global__ void add_f32_kernel(double2* __restrict__ x, const float2* __restrict__ d, int64_t n) {
@@ -201,16 +269,17 @@ __global__ void check_finite_kernel(const double2* __restrict__ a, int64_t n, in
 }  // namespace
 
 cudaError_t launch_raster_eps(const GridGeom& g, const double* widths, double* eps,
+                              const double2* dg0, const double2* kss, double2* dg,
                               int32_t* status, cudaStream_t s) {
-  dim3 blk(128), grd((unsigned)ceil_div(g.ny, 128), (unsigned)g.nx);
-  raster_kernel<<<grd, blk, 0, s>>>(g, widths, eps, status); rci_note_launch();
+  dim3 blk(64), grd((unsigned)ceil_div(g.ny, 64), (unsigned)g.nx);
+  raster_kernel<<<grd, blk, 0, s>>>(g, widths, eps, dg0, kss, dg, status); rci_note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_assemble(const GridGeom& g, const double* eps, double2* dg, double2* cx,
-                            double2* cy, cudaStream_t s) {
+cudaError_t launch_pml_coefficients(const GridGeom& g, double2* dg0, double2* kss, double2* cx,
+                                    double2* cy, cudaStream_t s) {
   dim3 blk(128), grd((unsigned)ceil_div(g.ny, 128), (unsigned)g.nx);
-  assemble_kernel<<<grd, blk, 0, s>>>(g, eps, dg, cx, cy); rci_note_launch();
+  pml_coeff_kernel<<<grd, blk, 0, s>>>(g, dg0, kss, cx, cy); rci_note_launch();
   return cudaGetLastError();
 }
 
@@ -230,6 +299,11 @@ int residual_blocks(const GridGeom& g) {
 cudaError_t launch_residual(const GridGeom& g, const double2* dg, const double2* cx,
                             const double2* cy, const double2* b, const double2* x, double2* r,
                             int nrhs, double* part_r, double* part_b, cudaStream_t s) {
+  if (nrhs == 1) {
+    residual1_kernel<<<RES_BLOCKS, RES_THREADS, 0, s>>>(g, dg, cx, cy, b, x, r, part_r, part_b);
+    rci_note_launch();
+    return cudaGetLastError();
+  }
   size_t smem = sizeof(double) * 2 * (RES_THREADS / 32) * (size_t)nrhs;
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   if (smem > 48 * 1024)
@@ -242,8 +316,8 @@ cudaError_t launch_residual(const GridGeom& g, const double2* dg, const double2*
 
 cudaError_t launch_ratio_norms(const double* part_r, const double* part_b, int nblk, int nrhs,
                                double* out, cudaStream_t s) {
-  ratio_norms_kernel<<<(unsigned)ceil_div(nrhs, 128), 128, 0, s>>>(part_r, part_b, nblk, nrhs,
-                                                                    out); rci_note_launch();
+  ratio_norms_kernel<<<(unsigned)nrhs, 256, 0, s>>>(part_r, part_b, nblk, nrhs, out);
+  rci_note_launch();
   return cudaGetLastError();
 }
 

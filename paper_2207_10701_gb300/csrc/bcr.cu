@@ -189,88 +189,188 @@ __global__ void level0_schur_kernel(const double2* __restrict__ dg, const double
 }
 
 // ===================================================================== Gauss-Jordan
-// In-place inversion with partial pivoting (largest |re|+|im| in the column, ties to
-// the lowest row).  Row interchanges are undone as column interchanges on output.
-// One block per matrix; the matrix lives in shared memory (SMEM) or in global memory
-// (the source slot, which is destroyed).
-constexpr int GJ_THREADS = 512;
+// Blocked in-place inversion with partial pivoting (largest |re|+|im| in the column,
+// ties to the lowest row).  For each panel of NB columns:
+//   1. NB unblocked Gauss-Jordan steps restricted to the panel columns (row swaps of the
+//      panel columns only, pivot rows scaled, other rows eliminated);
+//   2. the panel's row swaps, in order, applied to every other column;
+//   3. every other column updated at once by M, the product of the panel's elementary
+//      Gauss-Jordan transforms: M differs from the identity only in the panel columns,
+//      and the in-place algorithm leaves exactly M's columns there, so
+//      A_rest <- M A_rest = A_rest + M[:, panel] A_rest[panel rows] off the panel rows and
+//      M[panel, panel] A_rest[panel rows] on them.
+// Row interchanges are undone as column interchanges on output.  One block per matrix;
+// the matrix lives in shared memory (SMEM) or in global memory (the source slot, which
+// is destroyed); the panel rows of step 3 are staged in shared memory.
+constexpr int GJ_THREADS = 256;
+constexpr size_t SMEM_LIMIT = 227 * 1024;
 
-template <typename T, bool SMEM>
+template <typename T>
+struct GjSmem {
+  // byte offsets of the shared-memory regions for an n x n matrix and panel width nb
+  size_t coln, colk, rowk, tpanel, perm, idx, mat, total;
+  __host__ __device__ GjSmem(int n, int nb, bool smem_matrix) {
+    size_t e = sizeof(cplx<T>);
+    coln = 0;
+    colk = coln + (size_t)n * e;
+    rowk = colk + (size_t)n * e;
+    tpanel = rowk + (size_t)nb * e;
+    perm = tpanel + (size_t)nb * n * e;
+    idx = perm + (size_t)n * sizeof(int);
+    mat = (idx + (size_t)n * sizeof(int) + 15) & ~(size_t)15;
+    total = mat + (smem_matrix ? (size_t)n * n * e : 0);
+  }
+};
+
+template <typename T, bool SMEM, int NB, int TR, int TC>
 __global__ void __launch_bounds__(GJ_THREADS)
 gj_inverse_kernel(cplx<T>* __restrict__ src, int64_t src_stride, cplx<T>* __restrict__ out,
                   int64_t out_stride, int n, int32_t* status) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  cplx<T>* rowk = reinterpret_cast<cplx<T>*>(sm_raw);
-  cplx<T>* colk = rowk + n;
-  int* perm = reinterpret_cast<int*>(colk + n);
-  int* idx = perm + n;
-  cplx<T>* a_s = reinterpret_cast<cplx<T>*>(sm_raw + (((size_t)2 * n * sizeof(cplx<T>) +
-                                                         (size_t)2 * n * sizeof(int) + 15) &
-                                                        ~(size_t)15));
+  const GjSmem<T> L(n, NB, SMEM);
+  cplx<T>* coln = reinterpret_cast<cplx<T>*>(sm_raw + L.coln);    // column k before its swap
+  cplx<T>* colk = reinterpret_cast<cplx<T>*>(sm_raw + L.colk);    // column k after the swap
+  cplx<T>* rowk = reinterpret_cast<cplx<T>*>(sm_raw + L.rowk);    // scaled pivot row (panel)
+  cplx<T>* tp = reinterpret_cast<cplx<T>*>(sm_raw + L.tpanel);    // panel rows, other columns
+  int* perm = reinterpret_cast<int*>(sm_raw + L.perm);
+  int* idx = reinterpret_cast<int*>(sm_raw + L.idx);
   __shared__ int s_p;
-  __shared__ cplx<T> s_pinv, s_pv, s_akk;
+  __shared__ cplx<T> s_pinv;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nwarps = GJ_THREADS / 32;
   cplx<T>* g = src + (int64_t)blockIdx.x * src_stride;
-  cplx<T>* a = SMEM ? a_s : g;
+  cplx<T>* a = SMEM ? reinterpret_cast<cplx<T>*>(sm_raw + L.mat) : g;
   if (SMEM) {
     for (int e = tid; e < n * n; e += GJ_THREADS) a[e] = g[e];
-    __syncthreads();
   }
   bool sing = false;
-  for (int k = 0; k < n; ++k) {
-    if (warp == 0) {
-      T best = T(-1);
-      int bi = k;
-      for (int i = k + lane; i < n; i += 32) {
-        T v = cabs1(a[(int64_t)i * n + k]);
-        if (v > best) {
-          best = v;
-          bi = i;
+  for (int c0 = 0; c0 < n; c0 += NB) {
+    const int nb = n - c0 < NB ? n - c0 : NB;
+    __syncthreads();
+    for (int i = tid; i < n; i += GJ_THREADS) coln[i] = a[(int64_t)i * n + c0];
+    __syncthreads();
+    // ---------------- panel
+    for (int k = c0; k < c0 + nb; ++k) {
+      if (warp == 0) {
+        T best = T(-1);
+        int bi = k;
+        for (int i = k + lane; i < n; i += 32) {
+          T v = cabs1(coln[i]);
+          if (v > best) {
+            best = v;
+            bi = i;
+          }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+          T ob = __shfl_down_sync(0xffffffffu, best, off);
+          int oi = __shfl_down_sync(0xffffffffu, bi, off);
+          if (ob > best || (ob == best && oi < bi)) {
+            best = ob;
+            bi = oi;
+          }
+        }
+        if (lane == 0) {
+          s_p = bi;
+          if (!(best > T(0))) sing = true;
+          s_pinv = crecip(coln[bi]);
+          perm[k] = bi;
         }
       }
-      for (int off = 16; off > 0; off >>= 1) {
-        T ob = __shfl_down_sync(0xffffffffu, best, off);
-        int oi = __shfl_down_sync(0xffffffffu, bi, off);
-        if (ob > best || (ob == best && oi < bi)) {
-          best = ob;
-          bi = oi;
+      __syncthreads();
+      const int p = s_p;
+      const cplx<T> pinv = s_pinv;
+      for (int i = tid; i < n; i += GJ_THREADS) colk[i] = coln[i == k ? p : (i == p ? k : i)];
+      for (int t = tid; t < nb; t += GJ_THREADS) {
+        const int j = c0 + t;
+        cplx<T> rk = a[(int64_t)k * n + j];
+        cplx<T> rp = a[(int64_t)p * n + j];
+        cplx<T> v = (j == k ? mkc(T(1), T(0)) : rp) * pinv;
+        if (p != k) a[(int64_t)p * n + j] = rk;
+        a[(int64_t)k * n + j] = v;
+        rowk[t] = v;
+      }
+      __syncthreads();
+      const int knext = k + 1 - c0;  // panel column whose new values feed the next pivot search
+      for (int e = tid; e < n * nb; e += GJ_THREADS) {
+        const int i = e / nb, t = e - (e / nb) * nb;
+        const int j = c0 + t;
+        if (i != k) {
+          cplx<T> base = (j == k) ? czero<T>() : a[(int64_t)i * n + j];
+          cplx<T> v = cfms(colk[i], rowk[t], base);
+          a[(int64_t)i * n + j] = v;
+          if (t == knext) coln[i] = v;
+        } else if (t == knext) {
+          coln[i] = rowk[t];
         }
       }
-      if (lane == 0) {
-        s_p = bi;
-        cplx<T> pv = a[(int64_t)bi * n + k];
-        s_pv = pv;
-        s_akk = a[(int64_t)k * n + k];
-        if (!(best > T(0))) sing = true;
-        s_pinv = crecip(pv);
-        perm[k] = bi;
+      __syncthreads();
+    }
+    const int m = n - nb;
+    if (m == 0) continue;
+    // ---------------- panel row swaps on the other columns, in order
+    for (int jj = tid; jj < m; jj += GJ_THREADS) {
+      const int j = jj < c0 ? jj : jj + nb;
+      for (int t = 0; t < nb; ++t) {
+        const int r = c0 + t, p = perm[r];
+        if (p != r) {
+          cplx<T> x = a[(int64_t)r * n + j];
+          a[(int64_t)r * n + j] = a[(int64_t)p * n + j];
+          a[(int64_t)p * n + j] = x;
+        }
       }
     }
     __syncthreads();
-    const int p = s_p;
-    const cplx<T> pinv = s_pinv;
-    for (int t = tid; t < n; t += GJ_THREADS) {
-      colk[t] = (t == k) ? s_pv : (t == p ? s_akk : a[(int64_t)t * n + k]);
-      cplx<T> rk = a[(int64_t)k * n + t];
-      cplx<T> rp = a[(int64_t)p * n + t];
-      cplx<T> v = (t == k ? mkc(T(1), T(0)) : rp) * pinv;
-      if (p != k) a[(int64_t)p * n + t] = rk;
-      a[(int64_t)k * n + t] = v;
-      rowk[t] = v;
+    for (int e = tid; e < nb * m; e += GJ_THREADS) {
+      const int t = e / m, jj = e - (e / m) * m;
+      const int j = jj < c0 ? jj : jj + nb;
+      tp[e] = a[(int64_t)(c0 + t) * n + j];
     }
     __syncthreads();
-    for (int i = warp; i < n; i += nwarps) {
-      if (i == k) continue;
-      const cplx<T> ci = colk[i];
-      cplx<T>* ar = a + (int64_t)i * n;
-      for (int j = lane; j < n; j += 32) {
-        cplx<T> base = (j == k) ? czero<T>() : ar[j];
-        ar[j] = cfms(ci, rowk[j], base);
+    // ---------------- other columns: rows outside the panel get A += M tp (M's panel columns
+    // there equal Z's); panel rows get M tp directly -- forming (M - I) there would cancel
+    // catastrophically for diagonally dominant blocks (M_kk = 1/pivot).  Register tiles of
+    // TR x TC per thread (16 x 16 threads).
+    const int ty = tid >> 4, tx = tid & 15;
+    for (int r0 = 0; r0 < n; r0 += 16 * TR) {
+      for (int q0 = 0; q0 < m; q0 += 16 * TC) {
+        cplx<T> acc[TR][TC];
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+          for (int c = 0; c < TC; ++c) {
+            const int i = r0 + ty + 16 * r, jj = q0 + tx + 16 * c;
+            const int j = jj < c0 ? jj : jj + nb;
+            const bool panel_row = i >= c0 && i < c0 + nb;
+            acc[r][c] = (i < n && jj < m && !panel_row) ? a[(int64_t)i * n + j] : czero<T>();
+          }
+        for (int t = 0; t < nb; ++t) {
+          cplx<T> zv[TR], tv[TC];
+#pragma unroll
+          for (int r = 0; r < TR; ++r) {
+            const int i = r0 + ty + 16 * r;
+            zv[r] = i < n ? a[(int64_t)i * n + c0 + t] : czero<T>();
+          }
+#pragma unroll
+          for (int c = 0; c < TC; ++c) {
+            const int jj = q0 + tx + 16 * c;
+            tv[c] = jj < m ? tp[t * m + jj] : czero<T>();
+          }
+#pragma unroll
+          for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int c = 0; c < TC; ++c) acc[r][c] = cfma(zv[r], tv[c], acc[r][c]);
+        }
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+          for (int c = 0; c < TC; ++c) {
+            const int i = r0 + ty + 16 * r, jj = q0 + tx + 16 * c;
+            const int j = jj < c0 ? jj : jj + nb;
+            if (i < n && jj < m) a[(int64_t)i * n + j] = acc[r][c];
+          }
       }
     }
-    __syncthreads();
   }
+  __syncthreads();
   if (tid == 0) {
     for (int j = 0; j < n; ++j) idx[j] = j;
     for (int k = n - 1; k >= 0; --k) {
@@ -289,30 +389,33 @@ gj_inverse_kernel(cplx<T>* __restrict__ src, int64_t src_stride, cplx<T>* __rest
   }
 }
 
-template <typename T>
-size_t gj_smem_bytes(int n, bool smem_matrix) {
-  size_t head = (((size_t)2 * n * sizeof(cplx<T>) + (size_t)2 * n * sizeof(int) + 15) & ~(size_t)15);
-  return head + (smem_matrix ? (size_t)n * n * sizeof(cplx<T>) : 0);
+template <typename T, bool SMEM, int NB, int TR, int TC>
+cudaError_t launch_gj_cfg(cplx<T>* src, int64_t src_stride, cplx<T>* out, int64_t out_stride,
+                          int n, int batch, int32_t* status, cudaStream_t s) {
+  const GjSmem<T> L(n, NB, SMEM);
+  if (L.total > SMEM_LIMIT) return cudaErrorInvalidValue;
+  if (L.total > 48 * 1024)
+    RCI_CUDA_TRY(cudaFuncSetAttribute(gj_inverse_kernel<T, SMEM, NB, TR, TC>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+  gj_inverse_kernel<T, SMEM, NB, TR, TC><<<batch, GJ_THREADS, L.total, s>>>(src, src_stride, out,
+                                                                            out_stride, n, status);
+  rci_note_launch();
+  return cudaGetLastError();
 }
-
-constexpr size_t SMEM_LIMIT = 227 * 1024;
 
 template <typename T>
 cudaError_t launch_gj(cplx<T>* src, int64_t src_stride, cplx<T>* out, int64_t out_stride, int n,
                       int batch, int32_t* status, cudaStream_t s) {
   if (batch <= 0) return cudaSuccess;
-  size_t full = gj_smem_bytes<T>(n, true);
-  if (full <= SMEM_LIMIT) {
-    RCI_CUDA_TRY(cudaFuncSetAttribute(gj_inverse_kernel<T, true>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)full));
-    gj_inverse_kernel<T, true><<<batch, GJ_THREADS, full, s>>>(src, src_stride, out, out_stride, n,
-                                                               status); rci_note_launch();
-  } else {
-    size_t head = gj_smem_bytes<T>(n, false);
-    gj_inverse_kernel<T, false><<<batch, GJ_THREADS, head, s>>>(src, src_stride, out, out_stride,
-                                                                n, status); rci_note_launch();
+  if (GjSmem<T>(n, 16, true).total <= SMEM_LIMIT) {
+    if constexpr (sizeof(T) == 4)
+      return launch_gj_cfg<T, true, 16, 5, 9>(src, src_stride, out, out_stride, n, batch, status, s);
+    else
+      return launch_gj_cfg<T, true, 16, 4, 4>(src, src_stride, out, out_stride, n, batch, status, s);
   }
-  return cudaGetLastError();
+  if (GjSmem<T>(n, 16, false).total <= SMEM_LIMIT)
+    return launch_gj_cfg<T, false, 16, 4, 4>(src, src_stride, out, out_stride, n, batch, status, s);
+  return launch_gj_cfg<T, false, 8, 4, 4>(src, src_stride, out, out_stride, n, batch, status, s);
 }
 
 // ===================================================================== batched GEMM

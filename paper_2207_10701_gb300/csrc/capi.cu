@@ -26,6 +26,7 @@ struct rci_grid {
   double* widths = nullptr;
   double* eps = nullptr;
   double2 *dg = nullptr, *cx = nullptr, *cy = nullptr;
+  double2 *dg0 = nullptr, *kss = nullptr;  // design-independent parts of the diagonal
   BcrHandle* bcr = nullptr;
   bool has_design = false, factored = false;
   // single right-hand-side vectors (FP64) and FP32 shadows
@@ -431,7 +432,7 @@ rci_status rci_destroy_grid(rci_grid* g) {
   if (!g) return RCI_OK;
   DeviceGuard dg(g->device);
   if (g->s) cudaStreamSynchronize(g->s);
-  void* ps[] = {g->widths, g->eps, g->dg, g->cx, g->cy, g->b1, g->x1, g->r1, g->r32, g->d32,
+  void* ps[] = {g->widths, g->eps, g->dg, g->cx, g->cy, g->dg0, g->kss, g->b1, g->x1, g->r1, g->r32, g->d32,
                 g->crow, g->vsrc, g->lags, g->qpart, g->dscal, g->part_r, g->part_b, g->ratio,
                 g->vf_scratch, g->dstatus, g->mb, g->mx, g->mr, g->m32a, g->m32b, g->th_d,
                 g->wq_d, g->f_d};
@@ -482,6 +483,8 @@ rci_status rci_create_grid(const rci_grid_desc* desc, void* stream, rci_grid** o
   CKC(dalloc(g, &g->dg, sizeof(double2) * N));
   CKC(dalloc(g, &g->cx, sizeof(double2) * N));
   CKC(dalloc(g, &g->cy, sizeof(double2) * N));
+  CKC(dalloc(g, &g->dg0, sizeof(double2) * N));
+  CKC(dalloc(g, &g->kss, sizeof(double2) * N));
   CKC(dalloc(g, &g->b1, sizeof(double2) * N));
   CKC(dalloc(g, &g->x1, sizeof(double2) * N));
   CKC(dalloc(g, &g->r1, sizeof(double2) * N));
@@ -500,6 +503,7 @@ rci_status rci_create_grid(const rci_grid_desc* desc, void* stream, rci_grid** o
   CKC(dalloc(g, &g->vf_scratch, sizeof(double) * (2 * VF_ORDER + 6 * VF_NODES)));
   CKC(dalloc(g, &g->dstatus, sizeof(int32_t)));
   CKC(cudaMemsetAsync(g->cx, 0, sizeof(double2) * N, g->s));
+  CKC(launch_pml_coefficients(g->g, g->dg0, g->kss, g->cx, g->cy, g->s));
   for (auto& e : g->ev) CKC(cudaEventCreate(&e));
   size_t fb = 0;
   CKC(bcr_create(g->g.nx, g->g.ny, desc->prec, &g->bcr, &fb));
@@ -538,9 +542,9 @@ rci_status rci_set_design(rci_grid* g, const double* widths, int64_t n_cells, in
                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->s),
      "widths");
   {
-    ProfScope ps(&g->prof, PF_SETUP, g->s, 0.0, 64.0 * g->N, 2);
-    CK(launch_raster_eps(g->g, g->widths, g->eps, g->dstatus, g->s), "raster");
-    CK(launch_assemble(g->g, g->eps, g->dg, g->cx, g->cy, g->s), "assemble");
+    ProfScope ps(&g->prof, PF_SETUP, g->s, 0.0, 56.0 * g->N, 1);
+    CK(launch_raster_eps(g->g, g->widths, g->eps, g->dg0, g->kss, g->dg, g->dstatus, g->s),
+       "raster");
   }
   g->has_design = true;
   g->factored = false;
@@ -736,6 +740,20 @@ rci_status rci_apply_operator(rci_grid* g, const double* x, double* y) {
   DeviceGuard dg(g->device);
   CK(launch_apply_A(g->g, g->dg, g->cx, g->cy, (const double2*)x, (double2*)y, 1, g->s), "apply A");
   CK(cudaStreamSynchronize(g->s), "apply A");
+  return RCI_OK;
+}
+
+rci_status rci_set_refinement(rci_grid* g, double tol, int32_t max_steps) {
+  if (!g) return RCI_EINVAL;
+  if (!(tol > 0.0) || max_steps < 0 || max_steps > 100)
+    return fail(g, RCI_EINVAL, "need tol > 0 and 0 <= max_steps <= 100");
+  if (g->d.prec == RCI_FP64) {
+    g->tol64 = tol;
+    g->max_refine64 = max_steps;
+  } else {
+    g->tol32 = tol;
+    g->max_refine32 = max_steps + 1;  // counts the first FP32 solve
+  }
   return RCI_OK;
 }
 

@@ -11,10 +11,13 @@ struct GridGeom {
 };
 
 // assemble.cu
+// per design: eps raster and the diagonal dg = dg0 + eps * kss (widths checked -> *status)
 cudaError_t launch_raster_eps(const GridGeom& g, const double* widths_dev, double* eps,
+                              const double2* dg0, const double2* kss, double2* dg,
                               int32_t* status, cudaStream_t s);
-cudaError_t launch_assemble(const GridGeom& g, const double* eps, double2* dg, double2* cx,
-                            double2* cy, cudaStream_t s);
+// once per grid: design-independent stencil parts (PML stretch, couplings)
+cudaError_t launch_pml_coefficients(const GridGeom& g, double2* dg0, double2* kss, double2* cx,
+                                    double2* cy, cudaStream_t s);
 cudaError_t launch_apply_A(const GridGeom& g, const double2* dg, const double2* cx,
                            const double2* cy, const double2* x, double2* y, int nrhs,
                            cudaStream_t s);

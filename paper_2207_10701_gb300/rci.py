@@ -81,6 +81,7 @@ EXPORTED = {
                                  C.POINTER(C.c_int64), C.POINTER(C.c_size_t)]),
     "rci_set_design": (C.c_int, [_P, _P, C.c_int64, C.c_int]),
     "rci_factor": (C.c_int, [_P]),
+    "rci_set_refinement": (C.c_int, [_P, C.c_double, C.c_int32]),
     "rci_solve": (C.c_int, [_P, _P, _P, C.c_int64, C.POINTER(InfoC)]),
     "rci_solve_reciprocal": (C.c_int, [_P, C.POINTER(ObjectiveC), _P, _P, C.POINTER(InfoC)]),
     "rci_avg_intensity": (C.c_int, [_P, C.POINTER(ObjectiveC), C.POINTER(LightC), _D,
@@ -234,6 +235,9 @@ class Grid:
 
     def factor(self):
         _check(lib().rci_factor(self._h), self._h)
+
+    def set_refinement(self, tol: float, max_steps: int):
+        _check(lib().rci_set_refinement(self._h, tol, max_steps), self._h)
 
     def solve(self, b, nrhs: int = 1):
         """b: complex128 CUDA tensor of nx*ny*nrhs entries ([i][j][q]); returns x."""
