@@ -8,56 +8,89 @@
 namespace {
 
 // ===================================================================== level 0
+constexpr int TRI_WARPS = 2;
+
+template <typename T>
+__host__ __device__ size_t tri_smem_per_warp(int ny) {
+  return ((size_t)6 * ny * sizeof(cplx<T>) + (size_t)ny + 15) & ~(size_t)15;
+}
+
 // Pivoted LU of the tridiagonal diagonal block T_r of an eliminated row r = 2k+1
 // (Gaussian elimination with adjacent-row interchanges): multipliers dl, inverse
 // pivots dinv, first and second superdiagonals du, du2 of U, and swap flags piv.
+// One warp per row: the lanes stage the row's coefficients in shared memory, lane 0
+// runs the sequential elimination there, and the lanes write the factors out.
 template <typename T>
-__global__ void tri_factor_kernel(const double2* __restrict__ dg, const double2* __restrict__ cy,
-                                  int nx, int ny, int m0, cplx<T>* __restrict__ tdl,
-                                  cplx<T>* __restrict__ tdinv, cplx<T>* __restrict__ tdu,
-                                  cplx<T>* __restrict__ tdu2, uint8_t* __restrict__ tpiv,
-                                  int32_t* status) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= m0) return;
-  int64_t r = 2 * (int64_t)k + 1;
-  const double2* d = dg + r * ny;
-  const double2* o = cy + r * ny;  // o[j] couples j and j+1
-  int64_t base = (int64_t)k * ny;
-  cplx<T> cur_d = ccast<T>(d[0]);
-  cplx<T> cur_du = ny > 1 ? ccast<T>(o[0]) : czero<T>();
-  bool sing = false;
-  for (int j = 0; j < ny - 1; ++j) {
-    cplx<T> bs = ccast<T>(o[j]);
-    cplx<T> dnext = ccast<T>(d[j + 1]);
-    cplx<T> dunext = (j + 1 < ny - 1) ? ccast<T>(o[j + 1]) : czero<T>();
-    if (cabs1(cur_d) >= cabs1(bs)) {
-      if (cabs1(cur_d) == T(0)) sing = true;
-      cplx<T> m = bs * crecip(cur_d);
-      tdl[base + j] = m;
-      tdinv[base + j] = crecip(cur_d);
-      tdu[base + j] = cur_du;
-      tdu2[base + j] = czero<T>();
-      tpiv[base + j] = 0;
-      cur_d = dnext - m * cur_du;
-      cur_du = dunext;
-    } else {
-      cplx<T> m = cur_d * crecip(bs);
-      tdl[base + j] = m;
-      tdinv[base + j] = crecip(bs);
-      tdu[base + j] = dnext;
-      tdu2[base + j] = dunext;
-      tpiv[base + j] = 1;
-      cur_d = cur_du - m * dnext;
-      cur_du = -(m * dunext);
-    }
+__global__ void __launch_bounds__(32 * TRI_WARPS)
+tri_factor_kernel(const double2* __restrict__ dg, const double2* __restrict__ cy, int nx, int ny,
+                  int m0, cplx<T>* __restrict__ tdl, cplx<T>* __restrict__ tdinv,
+                  cplx<T>* __restrict__ tdu, cplx<T>* __restrict__ tdu2,
+                  uint8_t* __restrict__ tpiv, int32_t* status) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * TRI_WARPS + w;
+  if (k >= m0) return;  // whole warp
+  cplx<T>* d = reinterpret_cast<cplx<T>*>(sm_raw + (size_t)w * tri_smem_per_warp<T>(ny));
+  cplx<T>* o = d + ny;
+  cplx<T>* dl = o + ny;
+  cplx<T>* di = dl + ny;
+  cplx<T>* du = di + ny;
+  cplx<T>* du2 = du + ny;
+  uint8_t* pv = reinterpret_cast<uint8_t*>(du2 + ny);
+  const int64_t r = 2 * (int64_t)k + 1;
+  for (int j = lane; j < ny; j += 32) {
+    d[j] = ccast<T>(dg[r * ny + j]);
+    o[j] = ccast<T>(cy[r * ny + j]);  // o[j] couples j and j+1
   }
-  if (cabs1(cur_d) == T(0)) sing = true;
-  tdinv[base + ny - 1] = crecip(cur_d);
-  tdl[base + ny - 1] = czero<T>();
-  tdu[base + ny - 1] = czero<T>();
-  tdu2[base + ny - 1] = czero<T>();
-  tpiv[base + ny - 1] = 0;
-  if (sing) atomicCAS(status, DEV_OK, DEV_SINGULAR);
+  __syncwarp();
+  if (lane == 0) {
+    cplx<T> cur_d = d[0];
+    cplx<T> cur_du = ny > 1 ? o[0] : czero<T>();
+    bool sing = false;
+    for (int j = 0; j < ny - 1; ++j) {
+      const cplx<T> bs = o[j];
+      const cplx<T> dnext = d[j + 1];
+      const cplx<T> dunext = (j + 1 < ny - 1) ? o[j + 1] : czero<T>();
+      if (cabs1(cur_d) >= cabs1(bs)) {
+        if (cabs1(cur_d) == T(0)) sing = true;
+        const cplx<T> inv = crecip(cur_d);
+        const cplx<T> m = bs * inv;
+        dl[j] = m;
+        di[j] = inv;
+        du[j] = cur_du;
+        du2[j] = czero<T>();
+        pv[j] = 0;
+        cur_d = dnext - m * cur_du;
+        cur_du = dunext;
+      } else {
+        const cplx<T> inv = crecip(bs);
+        const cplx<T> m = cur_d * inv;
+        dl[j] = m;
+        di[j] = inv;
+        du[j] = dnext;
+        du2[j] = dunext;
+        pv[j] = 1;
+        cur_d = cur_du - m * dnext;
+        cur_du = -(m * dunext);
+      }
+    }
+    if (cabs1(cur_d) == T(0)) sing = true;
+    di[ny - 1] = crecip(cur_d);
+    dl[ny - 1] = czero<T>();
+    du[ny - 1] = czero<T>();
+    du2[ny - 1] = czero<T>();
+    pv[ny - 1] = 0;
+    if (sing) atomicCAS(status, DEV_OK, DEV_SINGULAR);
+  }
+  __syncwarp();
+  const int64_t base = (int64_t)k * ny;
+  for (int j = lane; j < ny; j += 32) {
+    tdl[base + j] = dl[j];
+    tdinv[base + j] = di[j];
+    tdu[base + j] = du[j];
+    tdu2[base + j] = du2[j];
+    tpiv[base + j] = pv[j];
+  }
 }
 
 template <typename T>
@@ -91,6 +124,7 @@ __device__ __forceinline__ void tri_forward(const TriRow<T>& f, int n, Rhs rhs, 
 template <typename T, typename Load, typename Emit>
 __device__ __forceinline__ void tri_backward(const TriRow<T>& f, int n, Load load, Emit emit) {
   cplx<T> g1 = czero<T>(), g2 = czero<T>();  // g_{j+1}, g_{j+2}
+#pragma unroll 4
   for (int j = n - 1; j >= 0; --j) {
     cplx<T> y = load(j);
     y = cfms(f.du[j], g1, y);
@@ -102,18 +136,38 @@ __device__ __forceinline__ void tri_backward(const TriRow<T>& f, int n, Load loa
   }
 }
 
+// Forward sweep for the unit vector e_b into column ycol (stride ny).
+template <typename T>
+__device__ __forceinline__ void tri_forward_unit(const TriRow<T>& f, int n, int b,
+                                                 cplx<T>* __restrict__ ycol, int ny) {
+  cplx<T> cur = b == 0 ? mkc(T(1), T(0)) : czero<T>();
+  for (int j = 0; j < n - 1; ++j) {
+    const cplx<T> nb = (j + 1 == b) ? mkc(T(1), T(0)) : czero<T>();
+    if (f.piv[j]) {
+      ycol[(int64_t)j * ny] = nb;
+      cur = cfms(f.dl[j], nb, cur);
+    } else {
+      ycol[(int64_t)j * ny] = cur;
+      cur = cfms(f.dl[j], cur, nb);
+    }
+  }
+  ycol[(int64_t)(n - 1) * ny] = cur;
+}
+
 // Dense Schur blocks of the first reduced system, one block per kept row e = 2k:
 //   D'_k = T_e - diag(cx[e-1]) T_{e-1}^{-1} diag(cx[e-1]) - diag(cx[e]) T_{e+1}^{-1} diag(cx[e])
 //   L'_k = -diag(cx[e-1]) T_{e-1}^{-1} diag(cx[e-2])
-// Thread b forms column b of T^{-1} by a tridiagonal solve with the unit vector e_b,
-// using the output column as its temporary.
+// Thread b forms column b of T^{-1} by a tridiagonal solve with the unit vector e_b; the
+// forward sweep goes to a separate scratch column so the backward sweep's loads do not
+// wait on its own stores.
 template <typename T>
 __global__ void level0_schur_kernel(const double2* __restrict__ dg, const double2* __restrict__ cx,
                                     const double2* __restrict__ cy, int nx, int ny, int m0,
                                     const cplx<T>* __restrict__ tdl, const cplx<T>* __restrict__ tdinv,
                                     const cplx<T>* __restrict__ tdu, const cplx<T>* __restrict__ tdu2,
                                     const uint8_t* __restrict__ tpiv, cplx<T>* __restrict__ Dn,
-                                    cplx<T>* __restrict__ Ln) {
+                                    cplx<T>* __restrict__ Ln, cplx<T>* __restrict__ scratch,
+                                    cplx<T>* __restrict__ G0) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   cplx<T>* sm = reinterpret_cast<cplx<T>*>(sm_raw);
   // [0,4ny): right factors, [4ny,8ny): left factors, then cxl2, cxl, cxr, dge, cye; piv bytes last
@@ -157,29 +211,34 @@ __global__ void level0_schur_kernel(const double2* __restrict__ dg, const double
   __syncthreads();
   const int b = threadIdx.x;
   if (b >= ny) return;
-  cplx<T>* Dcol = Dn + (int64_t)k * ny * ny + b;
-  cplx<T>* Lcol = Ln + (int64_t)k * ny * ny + b;
+  const int64_t nn = (int64_t)ny * ny;
+  cplx<T>* __restrict__ Dcol = Dn + (int64_t)k * nn + b;
+  cplx<T>* __restrict__ Lcol = Ln + (int64_t)k * nn + b;
+  cplx<T>* __restrict__ Ycol = scratch + (int64_t)k * nn + b;
+  cplx<T>* __restrict__ Gcol = G0 + (int64_t)k * nn + b;
   auto Te = [&](int a) -> cplx<T> {
     if (a == b) return dge[a];
     if (a == b - 1) return cye[a];
     if (a == b + 1) return cye[b];
     return czero<T>();
   };
-  auto unit = [&](int a) -> cplx<T> { return a == b ? mkc(T(1), T(0)) : czero<T>(); };
   if (has_r) {
     TriRow<T> f{R, R + ny, R + 2 * ny, R + 3 * ny, pivR};
-    tri_forward<T>(f, ny, unit, [&](int a, cplx<T> y) { Dcol[(int64_t)a * ny] = y; });
+    tri_forward_unit<T>(f, ny, b, Ycol, ny);
     const cplx<T> sb = cxr[b];
-    tri_backward<T>(f, ny, [&](int a) { return Dcol[(int64_t)a * ny]; },
-                    [&](int a, cplx<T> g) { Dcol[(int64_t)a * ny] = cfms(cxr[a] * g, sb, Te(a)); });
+    tri_backward<T>(f, ny, [&](int a) { return Ycol[(int64_t)a * ny]; },
+                    [&](int a, cplx<T> g) {
+                      Dcol[(int64_t)a * ny] = cfms(cxr[a] * g, sb, Te(a));
+                      Gcol[(int64_t)a * ny] = g;  // T_{e+1}^{-1}, kept for the solve
+                    });
   } else {
     for (int a = 0; a < ny; ++a) Dcol[(int64_t)a * ny] = Te(a);
   }
   if (has_l) {
     TriRow<T> f{Lf, Lf + ny, Lf + 2 * ny, Lf + 3 * ny, pivL};
-    tri_forward<T>(f, ny, unit, [&](int a, cplx<T> y) { Lcol[(int64_t)a * ny] = y; });
+    tri_forward_unit<T>(f, ny, b, Ycol, ny);
     const cplx<T> sl = cxl[b], sl2 = cxl2[b];
-    tri_backward<T>(f, ny, [&](int a) { return Lcol[(int64_t)a * ny]; },
+    tri_backward<T>(f, ny, [&](int a) { return Ycol[(int64_t)a * ny]; },
                     [&](int a, cplx<T> g) {
                       cplx<T> cg = cxl[a] * g;
                       Lcol[(int64_t)a * ny] = -(cg * sl2);
@@ -198,11 +257,13 @@ __global__ void level0_schur_kernel(const double2* __restrict__ dg, const double
 //      Gauss-Jordan transforms: M differs from the identity only in the panel columns,
 //      and the in-place algorithm leaves exactly M's columns there, so
 //      A_rest <- M A_rest = A_rest + M[:, panel] A_rest[panel rows] off the panel rows and
-//      M[panel, panel] A_rest[panel rows] on them.
-// Row interchanges are undone as column interchanges on output.  One block per matrix;
-// the matrix lives in shared memory (SMEM) or in global memory (the source slot, which
-// is destroyed); the panel rows of step 3 are staged in shared memory.
-constexpr int GJ_THREADS = 256;
+//      M[panel, panel] A_rest[panel rows] on them (forming M - I there instead would cancel
+//      catastrophically for diagonally dominant blocks, whose M_kk = 1/pivot).
+// Row interchanges are undone as column interchanges on output.  One block of NT threads
+// per matrix; the matrix lives in shared memory (SMEM) or in global memory (the source
+// slot, which is destroyed); the panel rows of step 3 are staged in shared memory, and
+// the column that feeds the next pivot search is kept contiguous (coln) so the search
+// reads without bank conflicts.
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 
 template <typename T>
@@ -222,10 +283,16 @@ struct GjSmem {
   }
 };
 
-template <typename T, bool SMEM, int NB, int TR, int TC>
-__global__ void __launch_bounds__(GJ_THREADS)
+// NT threads = (NT/32) x 32; the update tiles are TR rows (stride NT/32) x TC columns
+// (stride 32) per thread, so within a warp the panel-column reads broadcast and the
+// staged-row reads are consecutive.
+template <typename T, bool SMEM, int NB, int TR, int TC, int NT>
+__global__ void __launch_bounds__(NT)
 gj_inverse_kernel(cplx<T>* __restrict__ src, int64_t src_stride, cplx<T>* __restrict__ out,
                   int64_t out_stride, int n, int32_t* status) {
+  static_assert((NB & (NB - 1)) == 0 && NB <= 32, "panel width: power of two <= 32");
+  constexpr int TY = NT / 32;
+  constexpr int LNB = NB == 32 ? 5 : NB == 16 ? 4 : NB == 8 ? 3 : NB == 4 ? 2 : NB == 2 ? 1 : 0;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const GjSmem<T> L(n, NB, SMEM);
   cplx<T>* coln = reinterpret_cast<cplx<T>*>(sm_raw + L.coln);    // column k before its swap
@@ -240,13 +307,13 @@ gj_inverse_kernel(cplx<T>* __restrict__ src, int64_t src_stride, cplx<T>* __rest
   cplx<T>* g = src + (int64_t)blockIdx.x * src_stride;
   cplx<T>* a = SMEM ? reinterpret_cast<cplx<T>*>(sm_raw + L.mat) : g;
   if (SMEM) {
-    for (int e = tid; e < n * n; e += GJ_THREADS) a[e] = g[e];
+    for (int e = tid; e < n * n; e += NT) a[e] = g[e];
   }
   bool sing = false;
   for (int c0 = 0; c0 < n; c0 += NB) {
     const int nb = n - c0 < NB ? n - c0 : NB;
     __syncthreads();
-    for (int i = tid; i < n; i += GJ_THREADS) coln[i] = a[(int64_t)i * n + c0];
+    for (int i = tid; i < n; i += NT) coln[i] = a[i * n + c0];
     __syncthreads();
     // ---------------- panel
     for (int k = c0; k < c0 + nb; ++k) {
@@ -260,6 +327,7 @@ gj_inverse_kernel(cplx<T>* __restrict__ src, int64_t src_stride, cplx<T>* __rest
             bi = i;
           }
         }
+#pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
           T ob = __shfl_down_sync(0xffffffffu, best, off);
           int oi = __shfl_down_sync(0xffffffffu, bi, off);
@@ -278,25 +346,27 @@ gj_inverse_kernel(cplx<T>* __restrict__ src, int64_t src_stride, cplx<T>* __rest
       __syncthreads();
       const int p = s_p;
       const cplx<T> pinv = s_pinv;
-      for (int i = tid; i < n; i += GJ_THREADS) colk[i] = coln[i == k ? p : (i == p ? k : i)];
-      for (int t = tid; t < nb; t += GJ_THREADS) {
-        const int j = c0 + t;
-        cplx<T> rk = a[(int64_t)k * n + j];
-        cplx<T> rp = a[(int64_t)p * n + j];
+      for (int i = tid; i < n; i += NT) colk[i] = coln[i == k ? p : (i == p ? k : i)];
+      if (tid < nb) {
+        const int j = c0 + tid;
+        cplx<T> rk = a[k * n + j];
+        cplx<T> rp = a[p * n + j];
         cplx<T> v = (j == k ? mkc(T(1), T(0)) : rp) * pinv;
-        if (p != k) a[(int64_t)p * n + j] = rk;
-        a[(int64_t)k * n + j] = v;
-        rowk[t] = v;
+        if (p != k) a[p * n + j] = rk;
+        a[k * n + j] = v;
+        rowk[tid] = v;
       }
       __syncthreads();
       const int knext = k + 1 - c0;  // panel column whose new values feed the next pivot search
-      for (int e = tid; e < n * nb; e += GJ_THREADS) {
-        const int i = e / nb, t = e - (e / nb) * nb;
+      const int kt = k - c0;
+      for (int e = tid; e < (n << LNB); e += NT) {
+        const int i = e >> LNB, t = e & (NB - 1);
+        if (t >= nb) continue;
         const int j = c0 + t;
         if (i != k) {
-          cplx<T> base = (j == k) ? czero<T>() : a[(int64_t)i * n + j];
+          cplx<T> base = (t == kt) ? czero<T>() : a[i * n + j];
           cplx<T> v = cfms(colk[i], rowk[t], base);
-          a[(int64_t)i * n + j] = v;
+          a[i * n + j] = v;
           if (t == knext) coln[i] = v;
         } else if (t == knext) {
           coln[i] = rowk[t];
@@ -306,52 +376,49 @@ gj_inverse_kernel(cplx<T>* __restrict__ src, int64_t src_stride, cplx<T>* __rest
     }
     const int m = n - nb;
     if (m == 0) continue;
-    // ---------------- panel row swaps on the other columns, in order
-    for (int jj = tid; jj < m; jj += GJ_THREADS) {
+    // ---------------- panel row swaps on the other columns, in order; stage panel rows
+    for (int jj = tid; jj < m; jj += NT) {
       const int j = jj < c0 ? jj : jj + nb;
       for (int t = 0; t < nb; ++t) {
         const int r = c0 + t, p = perm[r];
         if (p != r) {
-          cplx<T> x = a[(int64_t)r * n + j];
-          a[(int64_t)r * n + j] = a[(int64_t)p * n + j];
-          a[(int64_t)p * n + j] = x;
+          cplx<T> x = a[r * n + j];
+          a[r * n + j] = a[p * n + j];
+          a[p * n + j] = x;
         }
       }
     }
     __syncthreads();
-    for (int e = tid; e < nb * m; e += GJ_THREADS) {
-      const int t = e / m, jj = e - (e / m) * m;
-      const int j = jj < c0 ? jj : jj + nb;
-      tp[e] = a[(int64_t)(c0 + t) * n + j];
-    }
+    for (int t = 0; t < nb; ++t)
+      for (int jj = tid; jj < m; jj += NT) {
+        const int j = jj < c0 ? jj : jj + nb;
+        tp[t * m + jj] = a[(c0 + t) * n + j];
+      }
     __syncthreads();
-    // ---------------- other columns: rows outside the panel get A += M tp (M's panel columns
-    // there equal Z's); panel rows get M tp directly -- forming (M - I) there would cancel
-    // catastrophically for diagonally dominant blocks (M_kk = 1/pivot).  Register tiles of
-    // TR x TC per thread (16 x 16 threads).
-    const int ty = tid >> 4, tx = tid & 15;
-    for (int r0 = 0; r0 < n; r0 += 16 * TR) {
-      for (int q0 = 0; q0 < m; q0 += 16 * TC) {
+    // ---------------- other columns (register tiles TR x TC)
+    const int ty = warp, tx = lane;
+    for (int r0 = 0; r0 < n; r0 += TY * TR) {
+      for (int q0 = 0; q0 < m; q0 += 32 * TC) {
         cplx<T> acc[TR][TC];
 #pragma unroll
         for (int r = 0; r < TR; ++r)
 #pragma unroll
           for (int c = 0; c < TC; ++c) {
-            const int i = r0 + ty + 16 * r, jj = q0 + tx + 16 * c;
+            const int i = r0 + ty + TY * r, jj = q0 + tx + 32 * c;
             const int j = jj < c0 ? jj : jj + nb;
             const bool panel_row = i >= c0 && i < c0 + nb;
-            acc[r][c] = (i < n && jj < m && !panel_row) ? a[(int64_t)i * n + j] : czero<T>();
+            acc[r][c] = (i < n && jj < m && !panel_row) ? a[i * n + j] : czero<T>();
           }
         for (int t = 0; t < nb; ++t) {
           cplx<T> zv[TR], tv[TC];
 #pragma unroll
           for (int r = 0; r < TR; ++r) {
-            const int i = r0 + ty + 16 * r;
-            zv[r] = i < n ? a[(int64_t)i * n + c0 + t] : czero<T>();
+            const int i = r0 + ty + TY * r;
+            zv[r] = i < n ? a[i * n + c0 + t] : czero<T>();
           }
 #pragma unroll
           for (int c = 0; c < TC; ++c) {
-            const int jj = q0 + tx + 16 * c;
+            const int jj = q0 + tx + 32 * c;
             tv[c] = jj < m ? tp[t * m + jj] : czero<T>();
           }
 #pragma unroll
@@ -363,9 +430,9 @@ gj_inverse_kernel(cplx<T>* __restrict__ src, int64_t src_stride, cplx<T>* __rest
         for (int r = 0; r < TR; ++r)
 #pragma unroll
           for (int c = 0; c < TC; ++c) {
-            const int i = r0 + ty + 16 * r, jj = q0 + tx + 16 * c;
+            const int i = r0 + ty + TY * r, jj = q0 + tx + 32 * c;
             const int j = jj < c0 ? jj : jj + nb;
-            if (i < n && jj < m) a[(int64_t)i * n + j] = acc[r][c];
+            if (i < n && jj < m) a[i * n + j] = acc[r][c];
           }
       }
     }
@@ -383,22 +450,20 @@ gj_inverse_kernel(cplx<T>* __restrict__ src, int64_t src_stride, cplx<T>* __rest
   }
   __syncthreads();
   cplx<T>* o = out + (int64_t)blockIdx.x * out_stride;
-  for (int e = tid; e < n * n; e += GJ_THREADS) {
-    int i = e / n, j = e - (e / n) * n;
-    o[e] = a[(int64_t)i * n + idx[j]];
-  }
+  for (int i = 0; i < n; ++i)
+    for (int j = tid; j < n; j += NT) o[i * n + j] = a[i * n + idx[j]];
 }
 
-template <typename T, bool SMEM, int NB, int TR, int TC>
+template <typename T, bool SMEM, int NB, int TR, int TC, int NT>
 cudaError_t launch_gj_cfg(cplx<T>* src, int64_t src_stride, cplx<T>* out, int64_t out_stride,
                           int n, int batch, int32_t* status, cudaStream_t s) {
   const GjSmem<T> L(n, NB, SMEM);
   if (L.total > SMEM_LIMIT) return cudaErrorInvalidValue;
   if (L.total > 48 * 1024)
-    RCI_CUDA_TRY(cudaFuncSetAttribute(gj_inverse_kernel<T, SMEM, NB, TR, TC>,
+    RCI_CUDA_TRY(cudaFuncSetAttribute(gj_inverse_kernel<T, SMEM, NB, TR, TC, NT>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
-  gj_inverse_kernel<T, SMEM, NB, TR, TC><<<batch, GJ_THREADS, L.total, s>>>(src, src_stride, out,
-                                                                            out_stride, n, status);
+  gj_inverse_kernel<T, SMEM, NB, TR, TC, NT><<<batch, NT, L.total, s>>>(src, src_stride, out,
+                                                                        out_stride, n, status);
   rci_note_launch();
   return cudaGetLastError();
 }
@@ -407,15 +472,23 @@ template <typename T>
 cudaError_t launch_gj(cplx<T>* src, int64_t src_stride, cplx<T>* out, int64_t out_stride, int n,
                       int batch, int32_t* status, cudaStream_t s) {
   if (batch <= 0) return cudaSuccess;
-  if (GjSmem<T>(n, 16, true).total <= SMEM_LIMIT) {
-    if constexpr (sizeof(T) == 4)
-      return launch_gj_cfg<T, true, 16, 5, 9>(src, src_stride, out, out_stride, n, batch, status, s);
-    else
-      return launch_gj_cfg<T, true, 16, 4, 4>(src, src_stride, out, out_stride, n, batch, status, s);
+  if (n > 1024) return cudaErrorInvalidValue;
+  if constexpr (sizeof(T) == 4) {
+    if (GjSmem<T>(n, 16, true).total <= SMEM_LIMIT)
+      return launch_gj_cfg<T, true, 16, 5, 5, 512>(src, src_stride, out, out_stride, n, batch,
+                                                   status, s);
+    return launch_gj_cfg<T, false, 16, 5, 5, 512>(src, src_stride, out, out_stride, n, batch,
+                                                  status, s);
+  } else {
+    if (GjSmem<T>(n, 16, true).total <= SMEM_LIMIT)
+      return launch_gj_cfg<T, true, 16, 5, 5, 256>(src, src_stride, out, out_stride, n, batch,
+                                                   status, s);
+    if (GjSmem<T>(n, 16, false).total <= SMEM_LIMIT)
+      return launch_gj_cfg<T, false, 16, 5, 5, 256>(src, src_stride, out, out_stride, n, batch,
+                                                    status, s);
+    return launch_gj_cfg<T, false, 8, 5, 5, 256>(src, src_stride, out, out_stride, n, batch,
+                                                 status, s);
   }
-  if (GjSmem<T>(n, 16, false).total <= SMEM_LIMIT)
-    return launch_gj_cfg<T, false, 16, 4, 4>(src, src_stride, out, out_stride, n, batch, status, s);
-  return launch_gj_cfg<T, false, 8, 4, 4>(src, src_stride, out, out_stride, n, batch, status, s);
 }
 
 // ===================================================================== batched GEMM
@@ -554,6 +627,10 @@ cudaError_t gemm(int M, int N, int K, bool ta, bool tb, cplx<T> alpha, const cpl
   ProfScope ps(prof, fam, s, 8.0 * M * N * K * (double)batch,
                (double)sizeof(cplx<T>) * batch * ((double)M * K + (double)K * N + (double)M * N), 1);
   GemmArgs<T> a{M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, C0, ldc0, sC0, alpha, beta};
+  // small batches (the last reduction levels) leave most SMs idle with large tiles and
+  // are latency-bound: use 32 x 32 output tiles there
+  const int64_t big_tiles = (int64_t)batch * ceil_div(M, 80) * ceil_div(N, 80);
+  if (big_tiles < 2 * 152) return gemm_tn<T, 2, 2>(a, ta, tb, batch, s);
   switch (pick_tile(M)) {
     case 3: return gemm_m<T, 3>(a, ta, tb, batch, s);
     case 5: return gemm_m<T, 5>(a, ta, tb, batch, s);
@@ -666,17 +743,89 @@ __device__ __forceinline__ cplx<T> warp_sum(cplx<T> v) {
   return v;
 }
 
-// y = M x (M row-major ny x ny, x in shared memory); optional y = y0 - M x - M2 x2.
+// y = M x (M row-major ny x ny, x in shared memory).  FP32 rows of even length are read
+// two complex values per 16-byte load.
 template <typename T>
 __device__ void gemv_n(const cplx<T>* __restrict__ M, const cplx<T>* x, cplx<T>* y, int ny) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int a = warp; a < ny; a += GV_WARPS) {
     cplx<T> acc = czero<T>();
     const cplx<T>* Mr = M + (int64_t)a * ny;
-    for (int c = lane; c < ny; c += 32) acc = cfma(Mr[c], x[c], acc);
+    if constexpr (sizeof(T) == 4) {
+      if ((ny & 1) == 0) {
+        const float4* M4 = reinterpret_cast<const float4*>(Mr);
+        for (int c2 = lane; c2 < ny / 2; c2 += 32) {
+          const float4 v = __ldg(M4 + c2);
+          acc = cfma(mkc(v.x, v.y), x[2 * c2], acc);
+          acc = cfma(mkc(v.z, v.w), x[2 * c2 + 1], acc);
+        }
+      } else {
+        for (int c = lane; c < ny; c += 32) acc = cfma(Mr[c], x[c], acc);
+      }
+    } else {
+      for (int c = lane; c < ny; c += 32) acc = cfma(Mr[c], x[c], acc);
+    }
     acc = warp_sum<T>(acc);
     if (lane == 0) y[a] = acc;
   }
+}
+
+// Level 0 forward, one right-hand side: t0[k] = T_{2k+1}^{-1} b[2k+1] (stored inverses).
+template <typename T>
+__global__ void __launch_bounds__(GV_THREADS)
+fwd0_gemv_kernel(const cplx<T>* __restrict__ G0, const cplx<T>* __restrict__ b,
+                 cplx<T>* __restrict__ t0, int ny) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cplx<T>* bs = reinterpret_cast<cplx<T>*>(sm_raw);
+  const int64_t k = blockIdx.x;
+  for (int c = threadIdx.x; c < ny; c += GV_THREADS) bs[c] = b[(2 * k + 1) * ny + c];
+  __syncthreads();
+  gemv_n<T>(G0 + k * ny * ny, bs, t0 + k * ny, ny);
+}
+
+// Level 0 backward, one right-hand side: x[2k] = x1[k];
+// x[2k+1] = T^{-1} (b[2k+1] - cx[2k] o x1[k] - cx[2k+1] o x1[k+1]).  b may alias x: row
+// 2k+1 of b is read into shared memory before row 2k+1 of x is written.
+template <typename T>
+__global__ void __launch_bounds__(GV_THREADS)
+bwd0_gemv_kernel(const cplx<T>* __restrict__ G0, const cplx<T>* b, const cplx<T>* __restrict__ x1,
+                 const double2* __restrict__ cx, cplx<T>* x, int nx, int ny) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cplx<T>* rhs = reinterpret_cast<cplx<T>*>(sm_raw);
+  const int64_t k = blockIdx.x, r = 2 * k + 1;
+  const bool has = r < nx, has_b = r + 1 < nx;
+  for (int c = threadIdx.x; c < ny; c += GV_THREADS) {
+    const cplx<T> xa = x1[k * ny + c];
+    if (has) {
+      cplx<T> v = cfms(ccast<T>(cx[(r - 1) * ny + c]), xa, b[r * ny + c]);
+      if (has_b) v = cfms(ccast<T>(cx[r * ny + c]), x1[(k + 1) * ny + c], v);
+      rhs[c] = v;
+    }
+    x[2 * k * ny + c] = xa;
+  }
+  __syncthreads();
+  if (has) gemv_n<T>(G0 + k * ny * ny, rhs, x + r * ny, ny);
+}
+
+// Level 0 backward, several right-hand sides: x[2k] = x1[k] and the right-hand sides of
+// the eliminated rows, tmp[k] = b[2k+1] - cx[2k] o x1[k] - cx[2k+1] o x1[k+1].
+template <typename T>
+__global__ void bwd0_rhs_kernel(const cplx<T>* b, const cplx<T>* __restrict__ x1,
+                                const double2* __restrict__ cx, cplx<T>* x,
+                                cplx<T>* __restrict__ tmp, int nx, int ny, int n1, int nrhs) {
+  const int64_t row = (int64_t)ny * nrhs;
+  const int64_t tt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tt >= (int64_t)n1 * row) return;
+  const int64_t k = tt / row, e = tt - k * row;
+  const int j = (int)(e / nrhs);
+  const int64_t r = 2 * k + 1;
+  const cplx<T> xa = x1[tt];
+  if (r < nx) {
+    cplx<T> v = cfms(ccast<T>(cx[(r - 1) * ny + j]), xa, b[r * row + e]);
+    if (r + 1 < nx) v = cfms(ccast<T>(cx[r * ny + j]), x1[(k + 1) * row + e], v);
+    tmp[k * row + e] = v;
+  }
+  x[2 * k * row + e] = xa;
 }
 
 // y = M^T x, columns spread over lanes, rows over warps, reduced through shared memory
@@ -772,6 +921,191 @@ final_gemv_kernel(const cplx<T>* __restrict__ Dinv, const cplx<T>* B, cplx<T>* x
   gemv_n<T>(Dinv, bs, x, ny);
 }
 
+
+// ----- single right-hand side, chunked: a block per (block row k, chunk of RC rows or
+// columns), so that even the last reduction levels spread over many SMs, and every lane
+// issues all of its 16-byte loads before it reduces.
+constexpr int RC = 32;
+constexpr int CH_THREADS = 256, CH_WARPS = CH_THREADS / 32;
+
+template <typename T> struct vec16;
+template <> struct vec16<float> { using type = float4; static constexpr int per = 2; };
+template <> struct vec16<double> { using type = double2; static constexpr int per = 1; };
+
+template <typename T>
+__device__ __forceinline__ cplx<T> dot_vec(const typename vec16<T>::type& v, const cplx<T>* x,
+                                           int c, cplx<T> acc) {
+  if constexpr (sizeof(T) == 4) {
+    acc = cfma(mkc(v.x, v.y), x[c], acc);
+    return cfma(mkc(v.z, v.w), x[c + 1], acc);
+  } else {
+    return cfma(v, x[c], acc);
+  }
+}
+
+// out[r] (= sub[r] -) M[r, :] x  for the RC rows r0 .. r0+RC-1 (x in shared memory).
+// Warp w handles rows r0 + w + CH_WARPS i; SMAX 16-byte vectors per lane and row.
+template <typename T, int SMAX>
+__device__ __forceinline__ void rows_mv(const cplx<T>* __restrict__ M, const cplx<T>* x, int ny,
+                                        int r0, cplx<T>* out, const cplx<T>* sub) {
+  using V = typename vec16<T>::type;
+  constexpr int PER = vec16<T>::per;
+  constexpr int RPW = RC / CH_WARPS;  // rows per warp
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nv = ny / PER;            // ny is a multiple of PER (checked by the launcher)
+  V v[RPW][SMAX];
+#pragma unroll
+  for (int i = 0; i < RPW; ++i) {
+    const int r = r0 + warp + CH_WARPS * i;
+    const V* Mr = reinterpret_cast<const V*>(M + (int64_t)r * ny);
+#pragma unroll
+    for (int s = 0; s < SMAX; ++s) {
+      const int q = lane + 32 * s;
+      if (r < ny && q < nv) v[i][s] = __ldg(Mr + q);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < RPW; ++i) {
+    const int r = r0 + warp + CH_WARPS * i;
+    cplx<T> acc = czero<T>();
+#pragma unroll
+    for (int s = 0; s < SMAX; ++s) {
+      const int q = lane + 32 * s;
+      if (r < ny && q < nv) acc = dot_vec<T>(v[i][s], x, PER * q, acc);
+    }
+    acc = warp_sum<T>(acc);
+    if (lane == 0 && r < ny) out[r] = sub ? sub[r] - acc : acc;
+  }
+}
+
+// out[c] = sum_a M[a][c] x[a] for the RC columns c0 .. c0+RC-1 (x in shared memory);
+// lanes own columns, warps stride over rows, partial sums reduced through red[CH_WARPS][RC].
+template <typename T>
+__device__ __forceinline__ void cols_mvT(const cplx<T>* __restrict__ M, const cplx<T>* x, int ny,
+                                         int c0, cplx<T>* red, cplx<T>* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = c0 + lane;
+  cplx<T> acc = czero<T>();
+  constexpr int U = 5;
+  for (int a0 = warp; a0 < ny; a0 += CH_WARPS * U) {
+    cplx<T> m[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int a = a0 + CH_WARPS * u;
+      m[u] = (a < ny && c < ny) ? __ldg(M + (int64_t)a * ny + c) : czero<T>();
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int a = a0 + CH_WARPS * u;
+      if (a < ny) acc = cfma(m[u], x[a], acc);
+    }
+  }
+  red[warp * RC + lane] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    cplx<T> s = czero<T>();
+#pragma unroll
+    for (int w = 0; w < CH_WARPS; ++w) s = s + red[w * RC + lane];
+    if (c < ny) out[c] = s;
+  }
+  __syncthreads();
+}
+
+// Dense level, forward: t_k = Dinv_k b_{2k+1} (rows of chunk), P_k = X_k^T b_{2k+1},
+// Q_k = Y_k^T b_{2k+1} (columns of chunk).  Grid (m, ceil(ny / RC)).
+template <typename T, int SMAX>
+__global__ void __launch_bounds__(CH_THREADS)
+fwd_chunk_kernel(const cplx<T>* __restrict__ Dinv, const cplx<T>* __restrict__ X,
+                 const cplx<T>* __restrict__ Y, const cplx<T>* __restrict__ B,
+                 cplx<T>* __restrict__ t, cplx<T>* __restrict__ P, cplx<T>* __restrict__ Q, int n,
+                 int ny) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cplx<T>* bs = reinterpret_cast<cplx<T>*>(sm_raw);
+  cplx<T>* red = bs + ny;
+  const int64_t k = blockIdx.x;
+  const int c0 = blockIdx.y * RC;
+  const int64_t nn = (int64_t)ny * ny;
+  for (int c = threadIdx.x; c < ny; c += CH_THREADS) bs[c] = B[(2 * k + 1) * ny + c];
+  __syncthreads();
+  rows_mv<T, SMAX>(Dinv + k * nn, bs, ny, c0, t + k * ny, nullptr);
+  cols_mvT<T>(X + k * nn, bs, ny, c0, red, P + k * ny);
+  if (2 * k + 2 < n) cols_mvT<T>(Y + k * nn, bs, ny, c0, red, Q + k * ny);
+}
+
+// Dense level, backward: x_l[2k] = x_up[k];
+// x_l[2k+1] = t_k - X_k x_up[k] - Y_k x_up[k+1] (rows of chunk).  Grid (nk, ceil(ny / RC)).
+template <typename T, int SMAX>
+__global__ void __launch_bounds__(CH_THREADS)
+bwd_chunk_kernel(const cplx<T>* __restrict__ X, const cplx<T>* __restrict__ Y,
+                 const cplx<T>* __restrict__ t, const cplx<T>* __restrict__ xup,
+                 cplx<T>* __restrict__ xl, int n, int m, int ny) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cplx<T>* xa = reinterpret_cast<cplx<T>*>(sm_raw);
+  cplx<T>* xb = xa + ny;
+  cplx<T>* tmp = xb + ny;
+  const int64_t k = blockIdx.x;
+  const int c0 = blockIdx.y * RC;
+  const int64_t nn = (int64_t)ny * ny;
+  const bool has_b = 2 * k + 2 < n;
+  for (int c = threadIdx.x; c < ny; c += CH_THREADS) {
+    xa[c] = xup[k * ny + c];
+    xb[c] = has_b ? xup[(k + 1) * ny + c] : czero<T>();
+  }
+  for (int c = c0 + threadIdx.x; c < c0 + RC && c < ny; c += CH_THREADS)
+    xl[2 * k * ny + c] = xup[k * ny + c];
+  __syncthreads();
+  if (k >= m) return;
+  // tmp = t - X xa on the chunk rows, then x = tmp - Y xb
+  rows_mv<T, SMAX>(X + k * nn, xa, ny, c0, tmp, t + k * ny);
+  __syncthreads();
+  if (has_b) {
+    rows_mv<T, SMAX>(Y + k * nn, xb, ny, c0, xl + (2 * k + 1) * ny, tmp);
+  } else {
+    for (int c = c0 + threadIdx.x; c < c0 + RC && c < ny; c += CH_THREADS)
+      xl[(2 * k + 1) * ny + c] = tmp[c];
+  }
+}
+
+// y_k = M_k v_k for stored inverses (level 0 forward, the last single row): the vector
+// is row vrow of V (stride ny).  Grid (batch, ceil(ny / RC)).
+template <typename T, int SMAX>
+__global__ void __launch_bounds__(CH_THREADS)
+mv_chunk_kernel(const cplx<T>* __restrict__ M, const cplx<T>* __restrict__ V, int64_t v_stride,
+                int64_t v_off, cplx<T>* __restrict__ y, int ny) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cplx<T>* vs = reinterpret_cast<cplx<T>*>(sm_raw);
+  const int64_t k = blockIdx.x;
+  for (int c = threadIdx.x; c < ny; c += CH_THREADS) vs[c] = V[k * v_stride + v_off + c];
+  __syncthreads();
+  rows_mv<T, SMAX>(M + k * (int64_t)ny * ny, vs, ny, blockIdx.y * RC, y + k * ny, nullptr);
+}
+
+// Level 0 backward with stored inverses: x[2k] = x1[k];
+// x[2k+1] = G_k (b[2k+1] - cx[2k] o x1[k] - cx[2k+1] o x1[k+1]) on the chunk rows.
+// b must not alias x (other blocks of the same k still read row 2k+1 of b).
+template <typename T, int SMAX>
+__global__ void __launch_bounds__(CH_THREADS)
+bwd0_chunk_kernel(const cplx<T>* __restrict__ G0, const cplx<T>* __restrict__ b,
+                  const cplx<T>* __restrict__ x1, const double2* __restrict__ cx,
+                  cplx<T>* __restrict__ x, int nx, int ny) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cplx<T>* rhs = reinterpret_cast<cplx<T>*>(sm_raw);
+  const int64_t k = blockIdx.x, r = 2 * k + 1;
+  const int c0 = blockIdx.y * RC;
+  const bool has = r < nx, has_b = r + 1 < nx;
+  for (int c = threadIdx.x; c < ny; c += CH_THREADS) {
+    if (has) {
+      cplx<T> v = cfms(ccast<T>(cx[(r - 1) * ny + c]), x1[k * ny + c], b[r * ny + c]);
+      if (has_b) v = cfms(ccast<T>(cx[r * ny + c]), x1[(k + 1) * ny + c], v);
+      rhs[c] = v;
+    }
+  }
+  for (int c = c0 + threadIdx.x; c < c0 + RC && c < ny; c += CH_THREADS)
+    x[2 * k * ny + c] = x1[k * ny + c];
+  __syncthreads();
+  if (has) rows_mv<T, SMAX>(G0 + k * (int64_t)ny * ny, rhs, ny, c0, x + r * ny, nullptr);
+}
+
 }  // namespace
 
 // ===================================================================== handle
@@ -786,6 +1120,7 @@ struct BcrHandle {
   // factor storage
   void *tdl = nullptr, *tdinv = nullptr, *tdu = nullptr, *tdu2 = nullptr;
   uint8_t* tpiv = nullptr;
+  void* G0 = nullptr;             // dense T_r^{-1} of the level-0 eliminated rows (m0 x ny x ny)
   void* Dw[2] = {nullptr, nullptr};
   void* Lw[2] = {nullptr, nullptr};
   void* store = nullptr;
@@ -807,7 +1142,7 @@ static void free_ws(BcrHandle* h) {
 
 void bcr_destroy(BcrHandle* h) {
   if (!h) return;
-  void* ps[] = {h->tdl, h->tdinv, h->tdu, h->tdu2, h->tpiv, h->Dw[0], h->Dw[1],
+  void* ps[] = {h->tdl, h->tdinv, h->tdu, h->tdu2, h->tpiv, h->G0, h->Dw[0], h->Dw[1],
                 h->Lw[0], h->Lw[1], h->store, h->status};
   for (void* p : ps)
     if (p) cudaFree(p);
@@ -862,6 +1197,7 @@ cudaError_t bcr_create(int nx, int ny, int prec, BcrHandle** out, size_t* bytes)
   alloc(&h->tdu, m0b * h->esz);
   alloc(&h->tdu2, m0b * h->esz);
   alloc((void**)&h->tpiv, m0b);
+  alloc(&h->G0, m0b * ny * h->esz);
   for (int i = 0; i < 2; ++i) {
     alloc(&h->Dw[i], (size_t)n1 * nn * h->esz);
     alloc(&h->Lw[i], (size_t)n1 * nn * h->esz);
@@ -897,8 +1233,13 @@ static cudaError_t factor_t(BcrHandle* h, const double2* dg, const double2* cx, 
   ProfScope* l0 = new ProfScope(h->prof, PF_LEVEL0, s, 48.0 * ny * (double)ny * n1,
                                 2.0 * n1 * (double)nn * sizeof(cplx<T>), 2);
   if (m0 > 0) {
-    tri_factor_kernel<T><<<(unsigned)ceil_div(m0, 128), 128, 0, s>>>(dg, cy, nx, ny, m0, tdl, tdinv,
-                                                                    tdu, tdu2, h->tpiv, h->status); rci_note_launch();
+    size_t tsm = TRI_WARPS * tri_smem_per_warp<T>(ny);
+    if (tsm > 48 * 1024)
+      RCI_CUDA_TRY(cudaFuncSetAttribute(tri_factor_kernel<T>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+    tri_factor_kernel<T><<<(unsigned)ceil_div(m0, TRI_WARPS), 32 * TRI_WARPS, tsm, s>>>(
+        dg, cy, nx, ny, m0, tdl, tdinv, tdu, tdu2, h->tpiv, h->status);
+    rci_note_launch();
     RCI_CUDA_TRY(cudaGetLastError());
   }
   {
@@ -907,8 +1248,11 @@ static cudaError_t factor_t(BcrHandle* h, const double2* dg, const double2* cx, 
     if (smem > 48 * 1024)
       RCI_CUDA_TRY(cudaFuncSetAttribute(level0_schur_kernel<T>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // the next level's working D array is free during level 0 and serves as scratch
     level0_schur_kernel<T><<<n1, thr, smem, s>>>(dg, cx, cy, nx, ny, m0, tdl, tdinv, tdu, tdu2,
-                                                 h->tpiv, (cplx<T>*)h->Dw[0], (cplx<T>*)h->Lw[0]); rci_note_launch();
+                                                 h->tpiv, (cplx<T>*)h->Dw[0], (cplx<T>*)h->Lw[0],
+                                                 (cplx<T>*)h->Dw[1], (cplx<T>*)h->G0);
+    rci_note_launch();
     RCI_CUDA_TRY(cudaGetLastError());
   }
   delete l0;
@@ -1006,79 +1350,119 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
   p += m1 * row;
   cplx<T>* xf = p;
 
-  auto tdl = (const cplx<T>*)h->tdl;
-  auto tdinv = (const cplx<T>*)h->tdinv;
-  auto tdu = (const cplx<T>*)h->tdu;
-  auto tdu2 = (const cplx<T>*)h->tdu2;
   auto store = (const cplx<T>*)h->store;
+  const cplx<T>* G0 = (const cplx<T>*)h->G0;
   const cplx<T> one = mkc(T(1), T(0)), mone = mkc(T(-1), T(0)), zero = czero<T>();
 
-  double sbytes = 0.0, sflops = 0.0;
+  double sbytes = 2.0 * m0 * (double)nn * sizeof(cplx<T>), sflops = 2.0 * 8.0 * m0 * (double)nn * nrhs;
   for (int l = 1; l < h->Lf; ++l) {
     sbytes += 5.0 * h->m[l] * (double)nn * sizeof(cplx<T>);
     sflops += 5.0 * 8.0 * h->m[l] * (double)nn * nrhs;
   }
   sbytes += (double)nn * sizeof(cplx<T>) + 2.0 * nx * (double)ny * nrhs * sizeof(cplx<T>);
   ProfScope ps(h->prof, PF_SOLVE, s, sflops, sbytes, 0);
-  // ---- level 0 forward
-  if (m0 > 0) {
-    int64_t nt = (int64_t)m0 * nrhs;
-    fwd0_kernel<T><<<(unsigned)ceil_div(nt, 128), 128, 0, s>>>(b, t0, ny, m0, nrhs, tdl, tdinv,
-                                                                tdu, tdu2, h->tpiv); rci_note_launch();
-    RCI_CUDA_TRY(cudaGetLastError());
+
+  if (nrhs == 1) {
+    if (ny % vec16<T>::per != 0 || ny > 256 * vec16<T>::per)
+      return cudaErrorInvalidValue;  // (grid creation keeps ny within these limits)
+    const int smax = (int)ceil_div(ny, 32 * vec16<T>::per);
+    const unsigned nch = (unsigned)ceil_div(ny, RC);
+    const size_t red_smem = (size_t)CH_WARPS * RC * sizeof(cplx<T>);
+#define RCI_SMAX_DISPATCH(KERNEL, GRID, SMEM, ...)                                   \
+  do {                                                                               \
+    switch (smax) {                                                                  \
+      case 1: KERNEL<T, 1><<<GRID, CH_THREADS, SMEM, s>>>(__VA_ARGS__); break;       \
+      case 2: KERNEL<T, 2><<<GRID, CH_THREADS, SMEM, s>>>(__VA_ARGS__); break;       \
+      case 3: KERNEL<T, 3><<<GRID, CH_THREADS, SMEM, s>>>(__VA_ARGS__); break;       \
+      case 4: KERNEL<T, 4><<<GRID, CH_THREADS, SMEM, s>>>(__VA_ARGS__); break;       \
+      case 5: KERNEL<T, 5><<<GRID, CH_THREADS, SMEM, s>>>(__VA_ARGS__); break;       \
+      case 6: KERNEL<T, 6><<<GRID, CH_THREADS, SMEM, s>>>(__VA_ARGS__); break;       \
+      case 7: KERNEL<T, 7><<<GRID, CH_THREADS, SMEM, s>>>(__VA_ARGS__); break;       \
+      default: KERNEL<T, 8><<<GRID, CH_THREADS, SMEM, s>>>(__VA_ARGS__); break;      \
+    }                                                                                \
+    rci_note_launch();                                                               \
+    RCI_CUDA_TRY(cudaGetLastError());                                                \
+  } while (0)
+    // the chunked level-0 backward pass reads b while other blocks write x: no aliasing
+    const cplx<T>* bsrc = b;
+    if ((const void*)b == (const void*)x) return cudaErrorInvalidValue;
+    // ---- level 0 forward: t0[k] = T_{2k+1}^{-1} b[2k+1]
+    if (m0 > 0)
+      RCI_SMAX_DISPATCH(mv_chunk_kernel, dim3(m0, nch), ny * sizeof(cplx<T>), G0, bsrc,
+                        2 * (int64_t)ny, (int64_t)ny, t0, ny);
+    {
+      int64_t nt = (int64_t)n1 * row;
+      keep0_kernel<T><<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(bsrc, t0, cx, B[1], nx, ny, n1, 1);
+      rci_note_launch();
+      RCI_CUDA_TRY(cudaGetLastError());
+    }
+    // ---- dense levels forward
+    for (int l = 1; l < h->Lf; ++l) {
+      const int n = (int)h->n[l], m = (int)h->m[l], nk = (int)h->n[l + 1];
+      const cplx<T>* Dinv = store + h->off[l];
+      const cplx<T>* X = Dinv + (int64_t)m * nn;
+      const cplx<T>* Y = X + (int64_t)m * nn;
+      RCI_SMAX_DISPATCH(fwd_chunk_kernel, dim3(m, nch), ny * sizeof(cplx<T>) + red_smem, Dinv, X,
+                        Y, B[l], tl[l], P, Q, n, ny);
+      int64_t nt = (int64_t)nk * row;
+      keep_kernel<T><<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(B[l], P, Q, B[l + 1], m, nk, row);
+      rci_note_launch();
+      RCI_CUDA_TRY(cudaGetLastError());
+    }
+    // ---- single remaining row
+    RCI_SMAX_DISPATCH(mv_chunk_kernel, dim3(1, nch), ny * sizeof(cplx<T>), store + h->final_off,
+                      B[h->Lf], (int64_t)0, (int64_t)0, xf, ny);
+    RCI_CUDA_TRY(cudaMemcpyAsync(B[h->Lf], xf, row * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s));
+    // ---- dense levels backward (the solution of level l overwrites B[l])
+    for (int l = h->Lf - 1; l >= 1; --l) {
+      const int n = (int)h->n[l], m = (int)h->m[l], nk = (int)h->n[l + 1];
+      const cplx<T>* Dinv = store + h->off[l];
+      const cplx<T>* X = Dinv + (int64_t)m * nn;
+      const cplx<T>* Y = X + (int64_t)m * nn;
+      RCI_SMAX_DISPATCH(bwd_chunk_kernel, dim3(nk, nch), 3 * ny * sizeof(cplx<T>), X, Y, tl[l],
+                        B[l + 1], B[l], n, m, ny);
+    }
+    // ---- level 0 backward
+    RCI_SMAX_DISPATCH(bwd0_chunk_kernel, dim3(n1, nch), ny * sizeof(cplx<T>), G0, bsrc, B[1], cx,
+                      x, nx, ny);
+#undef RCI_SMAX_DISPATCH
+    return cudaSuccess;
   }
+
+  // ================= several right-hand sides: batched GEMMs per level
+  // ---- level 0 forward: t0[k] = T_{2k+1}^{-1} b[2k+1] with the stored inverses
+  if (m0 > 0)
+    RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, one, G0, ny, nn, b + row, nrhs, 2 * row, zero,
+                         nullptr, 0, 0, t0, nrhs, row, m0, s));
   {
     int64_t nt = (int64_t)n1 * row;
-    keep0_kernel<T><<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(b, t0, cx, B[1], nx, ny, n1, nrhs); rci_note_launch();
+    keep0_kernel<T><<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(b, t0, cx, B[1], nx, ny, n1, nrhs);
+    rci_note_launch();
     RCI_CUDA_TRY(cudaGetLastError());
   }
   // ---- dense levels forward
-  const int cmax8 = ny <= 256;
   for (int l = 1; l < h->Lf; ++l) {
     const int n = (int)h->n[l], m = (int)h->m[l], nk = (int)h->n[l + 1];
     const int my = (n - 1) / 2;
     const cplx<T>* Dinv = store + h->off[l];
     const cplx<T>* X = Dinv + (int64_t)m * nn;
     const cplx<T>* Y = X + (int64_t)m * nn;
-    if (nrhs == 1) {
-      size_t smem = (size_t)(1 + GV_WARPS) * ny * sizeof(cplx<T>);
-      if (cmax8) {
-        if (smem > 48 * 1024)
-          RCI_CUDA_TRY(cudaFuncSetAttribute(fwd_gemv_kernel<T, 8>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        fwd_gemv_kernel<T, 8><<<m, GV_THREADS, smem, s>>>(Dinv, X, Y, B[l], tl[l], P, Q, n, ny); rci_note_launch();
-      } else {
-        if (smem > 48 * 1024)
-          RCI_CUDA_TRY(cudaFuncSetAttribute(fwd_gemv_kernel<T, 32>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        fwd_gemv_kernel<T, 32><<<m, GV_THREADS, smem, s>>>(Dinv, X, Y, B[l], tl[l], P, Q, n, ny); rci_note_launch();
-      }
-      RCI_CUDA_TRY(cudaGetLastError());
-    } else {
-      const cplx<T>* Bodd = B[l] + row;
-      RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, one, Dinv, ny, nn, Bodd, nrhs, 2 * row, zero,
-                           nullptr, 0, 0, tl[l], nrhs, row, m, s));
-      RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, true, false, one, X, ny, nn, Bodd, nrhs, 2 * row, zero,
-                           nullptr, 0, 0, P, nrhs, row, m, s));
-      RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, true, false, one, Y, ny, nn, Bodd, nrhs, 2 * row, zero,
-                           nullptr, 0, 0, Q, nrhs, row, my, s));
-    }
+    const cplx<T>* Bodd = B[l] + row;
+    RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, one, Dinv, ny, nn, Bodd, nrhs, 2 * row, zero,
+                         nullptr, 0, 0, tl[l], nrhs, row, m, s));
+    RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, true, false, one, X, ny, nn, Bodd, nrhs, 2 * row, zero,
+                         nullptr, 0, 0, P, nrhs, row, m, s));
+    RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, true, false, one, Y, ny, nn, Bodd, nrhs, 2 * row, zero,
+                         nullptr, 0, 0, Q, nrhs, row, my, s));
     int64_t nt = (int64_t)nk * row;
-    keep_kernel<T><<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(B[l], P, Q, B[l + 1], m, nk, row); rci_note_launch();
+    keep_kernel<T><<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(B[l], P, Q, B[l + 1], m, nk, row);
+    rci_note_launch();
     RCI_CUDA_TRY(cudaGetLastError());
   }
   // ---- single remaining row
-  {
-    const cplx<T>* Df = store + h->final_off;
-    if (nrhs == 1) {
-      final_gemv_kernel<T><<<1, GV_THREADS, ny * sizeof(cplx<T>), s>>>(Df, B[h->Lf], xf, ny); rci_note_launch();
-      RCI_CUDA_TRY(cudaGetLastError());
-    } else {
-      RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, one, Df, ny, 0, B[h->Lf], nrhs, 0, zero,
-                           nullptr, 0, 0, xf, nrhs, 0, 1, s));
-    }
-    RCI_CUDA_TRY(cudaMemcpyAsync(B[h->Lf], xf, row * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s));
-  }
+  RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, one, store + h->final_off, ny, 0, B[h->Lf], nrhs,
+                       0, zero, nullptr, 0, 0, xf, nrhs, 0, 1, s));
+  RCI_CUDA_TRY(cudaMemcpyAsync(B[h->Lf], xf, row * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s));
   // ---- dense levels backward (the solution of level l overwrites B[l])
   for (int l = h->Lf - 1; l >= 1; --l) {
     const int n = (int)h->n[l], m = (int)h->m[l], nk = (int)h->n[l + 1];
@@ -1086,26 +1470,26 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
     const cplx<T>* Dinv = store + h->off[l];
     const cplx<T>* X = Dinv + (int64_t)m * nn;
     const cplx<T>* Y = X + (int64_t)m * nn;
-    if (nrhs == 1) {
-      bwd_gemv_kernel<T><<<nk, GV_THREADS, 2 * ny * sizeof(cplx<T>), s>>>(X, Y, tl[l], B[l + 1],
-                                                                          B[l], n, m, ny); rci_note_launch();
-      RCI_CUDA_TRY(cudaGetLastError());
-    } else {
-      int64_t nt = (int64_t)nk * row;
-      copy_kept_kernel<T><<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(B[l + 1], B[l], nk, row); rci_note_launch();
-      RCI_CUDA_TRY(cudaGetLastError());
-      RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, mone, X, ny, nn, B[l + 1], nrhs, row, one,
-                           tl[l], nrhs, row, B[l] + row, nrhs, 2 * row, m, s));
-      RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, mone, Y, ny, nn, B[l + 1] + row, nrhs, row,
-                           one, B[l] + row, nrhs, 2 * row, B[l] + row, nrhs, 2 * row, my, s));
-    }
-  }
-  // ---- level 0 backward
-  {
-    int64_t nt = (int64_t)n1 * nrhs;
-    bwd0_kernel<T><<<(unsigned)ceil_div(nt, 128), 128, 0, s>>>(b, B[1], cx, x, nx, ny, n1, nrhs,
-                                                                tdl, tdinv, tdu, tdu2, h->tpiv); rci_note_launch();
+    int64_t nt = (int64_t)nk * row;
+    copy_kept_kernel<T><<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(B[l + 1], B[l], nk, row);
+    rci_note_launch();
     RCI_CUDA_TRY(cudaGetLastError());
+    RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, mone, X, ny, nn, B[l + 1], nrhs, row, one,
+                         tl[l], nrhs, row, B[l] + row, nrhs, 2 * row, m, s));
+    RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, mone, Y, ny, nn, B[l + 1] + row, nrhs, row,
+                         one, B[l] + row, nrhs, 2 * row, B[l] + row, nrhs, 2 * row, my, s));
+  }
+  // ---- level 0 backward: x[2k+1] = T^{-1}(b[2k+1] - couplings x), stored inverses
+  {
+    int64_t nt = (int64_t)n1 * row;
+    // t0 (no longer needed) holds the eliminated rows' right-hand sides
+    bwd0_rhs_kernel<T><<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(b, B[1], cx, x, t0, nx, ny, n1,
+                                                                    nrhs);
+    rci_note_launch();
+    RCI_CUDA_TRY(cudaGetLastError());
+    if (m0 > 0)
+      RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, one, G0, ny, nn, t0, nrhs, row, zero,
+                           nullptr, 0, 0, x + row, nrhs, 2 * row, m0, s));
   }
   return cudaSuccess;
 }

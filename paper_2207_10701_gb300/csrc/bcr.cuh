@@ -30,7 +30,7 @@ size_t bcr_bytes(const BcrHandle* h);
 cudaError_t bcr_factor(BcrHandle* h, const double2* dg, const double2* cx, const double2* cy,
                        cudaStream_t s);
 // Solve A x = b for nrhs right-hand sides, [i][j][q] with leading dimension nrhs, in the
-// handle's precision (float2 or double2 buffers).  b and x may alias.
+// handle's precision (float2 or double2 buffers).  b and x must not overlap.
 cudaError_t bcr_solve(BcrHandle* h, const double2* cx, const void* b, void* x, int nrhs,
                       cudaStream_t s);
 // Device status word (DEV_OK / DEV_SINGULAR / DEV_NONFINITE), read synchronously.

@@ -251,6 +251,8 @@ rci_status ensure_multi(rci_grid* g, int nq) {
   if (g->d.prec == RCI_FP32_REFINE) {
     CK(dalloc(g, &g->m32a, n * sizeof(float2)), "multi-rhs buffers");
     CK(dalloc(g, &g->m32b, n * sizeof(float2)), "multi-rhs buffers");
+  } else {
+    CK(dalloc(g, &g->m32a, n * sizeof(double2)), "multi-rhs buffers");  // FP64 corrections
   }
   g->mq_cap = nq;
   return RCI_OK;
@@ -285,7 +287,8 @@ rci_status residual_ratio(rci_grid* g, const double2* b, const double2* x, doubl
 
 // Solve A x = b (FP64 in/out, device, nrhs columns) with the grid's factorisation and
 // iterative refinement on the FP64 stencil residual.  r, a32, b32 are scratch buffers of
-// the same size (a32/b32 complex64, only for FP32 grids).
+// the same length: complex64 for FP32 grids; for FP64 grids a32 is complex128 (the
+// correction) and b32 is unused.
 rci_status refined_solve(rci_grid* g, const double2* b, double2* x, double2* r, void* a32,
                          void* b32, int nrhs, rci_info* info) {
   const int64_t n = g->N * nrhs;
@@ -293,12 +296,13 @@ rci_status refined_solve(rci_grid* g, const double2* b, double2* x, double2* r, 
   int it = 0;
   rci_status st = RCI_OK;
   if (g->d.prec == RCI_FP64) {
+    double2* d = (double2*)a32;
     CK(bcr_solve(g->bcr, g->cx, b, x, nrhs, g->s), "solve");
     st = residual_ratio(g, b, x, r, nrhs, &worst);
     if (st != RCI_OK) return st;
     while (worst > g->tol64 && it < g->max_refine64) {
-      CK(bcr_solve(g->bcr, g->cx, r, r, nrhs, g->s), "refine solve");
-      CK(launch_axpy64(x, r, n, g->s), "refine update");
+      CK(bcr_solve(g->bcr, g->cx, r, d, nrhs, g->s), "refine solve");
+      CK(launch_axpy64(x, d, n, g->s), "refine update");
       ++it;
       st = residual_ratio(g, b, x, r, nrhs, &worst);
       if (st != RCI_OK) return st;
@@ -491,6 +495,8 @@ rci_status rci_create_grid(const rci_grid_desc* desc, void* stream, rci_grid** o
   if (desc->prec == RCI_FP32_REFINE) {
     CKC(dalloc(g, &g->r32, sizeof(float2) * N));
     CKC(dalloc(g, &g->d32, sizeof(float2) * N));
+  } else {
+    CKC(dalloc(g, &g->r32, sizeof(double2) * N));  // FP64 refinement corrections
   }
   CKC(dalloc(g, &g->crow, sizeof(double2) * ns));
   CKC(dalloc(g, &g->vsrc, sizeof(double2) * ns));
