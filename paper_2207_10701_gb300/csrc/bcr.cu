@@ -4,6 +4,7 @@
 #include <vector>
 
 #include "bcr.cuh"
+#include "tc_gemm.cuh"
 
 namespace {
 
@@ -621,7 +622,7 @@ cudaError_t gemm(int M, int N, int K, bool ta, bool tb, cplx<T> alpha, const cpl
                  int64_t lda, int64_t sA, const cplx<T>* B, int64_t ldb, int64_t sB, cplx<T> beta,
                  const cplx<T>* C0, int64_t ldc0, int64_t sC0, cplx<T>* C, int64_t ldc,
                  int64_t sC, int batch, cudaStream_t s, Profiler* prof = nullptr,
-                 int fam = PF_GEMM) {
+                 int fam = PF_GEMM, int32_t* status = nullptr) {
   if (batch <= 0) return cudaSuccess;
   if (batch > 65535) return cudaErrorInvalidValue;
   ProfScope ps(prof, fam, s, 8.0 * M * N * K * (double)batch,
@@ -630,6 +631,13 @@ cudaError_t gemm(int M, int N, int K, bool ta, bool tb, cplx<T> alpha, const cpl
   // small batches (the last reduction levels) leave most SMs idle with large tiles and
   // are latency-bound: use 32 x 32 output tiles there
   const int64_t big_tiles = (int64_t)batch * ceil_div(M, 80) * ceil_div(N, 80);
+  // FP32 products with enough tiles to fill the GPU run on the tensor cores (3xTF32)
+  if constexpr (sizeof(T) == 4) {
+    const int64_t tc_tiles = (int64_t)batch * ceil_div(M, 128) * ceil_div(N, 80);
+    if (status && tc_tiles >= 152)
+      return launch_tc_cgemm(M, N, K, ta, tb, alpha, A, lda, sA, B, ldb, sB, beta, C0, ldc0, sC0,
+                             C, ldc, sC, batch, status, s);
+  }
   if (big_tiles < 2 * 152) return gemm_tn<T, 2, 2>(a, ta, tb, batch, s);
   switch (pick_tile(M)) {
     case 3: return gemm_m<T, 3>(a, ta, tb, batch, s);
@@ -1276,18 +1284,18 @@ static cudaError_t factor_t(BcrHandle* h, const double2* dg, const double2* cx, 
     }
     // X_k = Dinv_k L_{2k+1};  Y_k = Dinv_k L_{2k+2}^T
     RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, false, one, Dinv, ny, nn, L + nn, ny, 2 * nn, zero,
-                         nullptr, 0, 0, X, ny, nn, m, s, h->prof));
+                         nullptr, 0, 0, X, ny, nn, m, s, h->prof, PF_GEMM, h->status));
     RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, true, one, Dinv, ny, nn, L + 2 * nn, ny, 2 * nn, zero,
-                         nullptr, 0, 0, Y, ny, nn, my, s, h->prof));
+                         nullptr, 0, 0, Y, ny, nn, my, s, h->prof, PF_GEMM, h->status));
     // D'_0 = D_0;  D'_k = D_{2k} - L_{2k} Y_{k-1} (k >= 1);  D'_k -= L_{2k+1}^T X_k (k < m)
     RCI_CUDA_TRY(cudaMemcpyAsync(Dn, D, nn * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s));
     RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, false, mone, L + 2 * nn, ny, 2 * nn, Y, ny, nn, one,
-                         D + 2 * nn, ny, 2 * nn, Dn + nn, ny, nn, nk - 1, s, h->prof));
+                         D + 2 * nn, ny, 2 * nn, Dn + nn, ny, nn, nk - 1, s, h->prof, PF_GEMM, h->status));
     RCI_CUDA_TRY(gemm<T>(ny, ny, ny, true, false, mone, L + nn, ny, 2 * nn, X, ny, nn, one, Dn, ny,
-                         nn, Dn, ny, nn, m, s, h->prof));
+                         nn, Dn, ny, nn, m, s, h->prof, PF_GEMM, h->status));
     // L'_k = -L_{2k} X_{k-1} (k >= 1)
     RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, false, mone, L + 2 * nn, ny, 2 * nn, X, ny, nn, zero,
-                         nullptr, 0, 0, Ln + nn, ny, nn, nk - 1, s, h->prof));
+                         nullptr, 0, 0, Ln + nn, ny, nn, nk - 1, s, h->prof, PF_GEMM, h->status));
     cur = 1 - cur;
   }
   // last single row
@@ -1433,7 +1441,7 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
   // ---- level 0 forward: t0[k] = T_{2k+1}^{-1} b[2k+1] with the stored inverses
   if (m0 > 0)
     RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, one, G0, ny, nn, b + row, nrhs, 2 * row, zero,
-                         nullptr, 0, 0, t0, nrhs, row, m0, s));
+                         nullptr, 0, 0, t0, nrhs, row, m0, s, nullptr, PF_SOLVE, h->status));
   {
     int64_t nt = (int64_t)n1 * row;
     keep0_kernel<T><<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(b, t0, cx, B[1], nx, ny, n1, nrhs);
@@ -1449,11 +1457,11 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
     const cplx<T>* Y = X + (int64_t)m * nn;
     const cplx<T>* Bodd = B[l] + row;
     RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, one, Dinv, ny, nn, Bodd, nrhs, 2 * row, zero,
-                         nullptr, 0, 0, tl[l], nrhs, row, m, s));
+                         nullptr, 0, 0, tl[l], nrhs, row, m, s, nullptr, PF_SOLVE, h->status));
     RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, true, false, one, X, ny, nn, Bodd, nrhs, 2 * row, zero,
-                         nullptr, 0, 0, P, nrhs, row, m, s));
+                         nullptr, 0, 0, P, nrhs, row, m, s, nullptr, PF_SOLVE, h->status));
     RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, true, false, one, Y, ny, nn, Bodd, nrhs, 2 * row, zero,
-                         nullptr, 0, 0, Q, nrhs, row, my, s));
+                         nullptr, 0, 0, Q, nrhs, row, my, s, nullptr, PF_SOLVE, h->status));
     int64_t nt = (int64_t)nk * row;
     keep_kernel<T><<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(B[l], P, Q, B[l + 1], m, nk, row);
     rci_note_launch();
@@ -1461,7 +1469,7 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
   }
   // ---- single remaining row
   RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, one, store + h->final_off, ny, 0, B[h->Lf], nrhs,
-                       0, zero, nullptr, 0, 0, xf, nrhs, 0, 1, s));
+                       0, zero, nullptr, 0, 0, xf, nrhs, 0, 1, s, nullptr, PF_SOLVE, h->status));
   RCI_CUDA_TRY(cudaMemcpyAsync(B[h->Lf], xf, row * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s));
   // ---- dense levels backward (the solution of level l overwrites B[l])
   for (int l = h->Lf - 1; l >= 1; --l) {
@@ -1475,9 +1483,9 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
     rci_note_launch();
     RCI_CUDA_TRY(cudaGetLastError());
     RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, mone, X, ny, nn, B[l + 1], nrhs, row, one,
-                         tl[l], nrhs, row, B[l] + row, nrhs, 2 * row, m, s));
+                         tl[l], nrhs, row, B[l] + row, nrhs, 2 * row, m, s, nullptr, PF_SOLVE, h->status));
     RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, mone, Y, ny, nn, B[l + 1] + row, nrhs, row,
-                         one, B[l] + row, nrhs, 2 * row, B[l] + row, nrhs, 2 * row, my, s));
+                         one, B[l] + row, nrhs, 2 * row, B[l] + row, nrhs, 2 * row, my, s, nullptr, PF_SOLVE, h->status));
   }
   // ---- level 0 backward: x[2k+1] = T^{-1}(b[2k+1] - couplings x), stored inverses
   {
@@ -1489,7 +1497,7 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
     RCI_CUDA_TRY(cudaGetLastError());
     if (m0 > 0)
       RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, one, G0, ny, nn, t0, nrhs, row, zero,
-                           nullptr, 0, 0, x + row, nrhs, 2 * row, m0, s));
+                           nullptr, 0, 0, x + row, nrhs, 2 * row, m0, s, nullptr, PF_SOLVE, h->status));
   }
   return cudaSuccess;
 }

@@ -326,6 +326,11 @@ rci_status refined_solve(rci_grid* g, const double2* b, double2* x, double2* r, 
     info->refine_iters = it;
     info->rel_residual = worst;
   }
+  if (nrhs > 1) {  // the multi-RHS solve runs tensor-core GEMMs with bounded waits
+    int32_t dst = 0;
+    CK(bcr_read_status(g->bcr, &dst, g->s), "solve status");
+    if (dst == DEV_TIMEOUT) return fail(g, RCI_ETIMEOUT, "a bounded tensor-core wait expired");
+  }
   double tol = g->d.prec == RCI_FP64 ? 1e-9 : g->tol32;
   if (worst > tol) return fail(g, RCI_ENOCONV, "iterative refinement did not converge");
   return RCI_OK;
@@ -572,6 +577,7 @@ rci_status rci_factor(rci_grid* g) {
     g->has_design = false;
     return fail(g, RCI_EINVAL, "a device width lies outside (0, period)");
   }
+  if (st == DEV_TIMEOUT) return fail(g, RCI_ETIMEOUT, "a bounded tensor-core wait expired");
   if (st == DEV_SINGULAR) return fail(g, RCI_ESINGULAR, "zero pivot in a diagonal block");
   g->factored = true;
   return RCI_OK;

@@ -60,7 +60,7 @@ __host__ __device__ __forceinline__ cplx<To> ccast(From v) {
 
 // ---------------------------------------------------------------- device status word
 // Kernels never trap.  They record the first failure here and the host reads it.
-enum : int32_t { DEV_OK = 0, DEV_SINGULAR = 1, DEV_NONFINITE = 2, DEV_BADINPUT = 3 };
+enum : int32_t { DEV_OK = 0, DEV_SINGULAR = 1, DEV_NONFINITE = 2, DEV_BADINPUT = 3, DEV_TIMEOUT = 4 };
 
 // ---------------------------------------------------------------- launch helpers
 #define RCI_CUDA_TRY(expr)                                  \

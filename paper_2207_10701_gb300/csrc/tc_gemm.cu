@@ -1,0 +1,354 @@
+// Batched complex FP32 GEMM on the 5th-generation tensor cores (tcgen05, kind::tf32).
+//
+//   C[z] = alpha op(A[z]) op(B[z]) + beta C0[z]      (row-major, op = N or T, complex)
+//
+// Complex product as one real product: with interleaved storage a complex M x K matrix
+// A is already the real M x 2K matrix [re im re im ...]; B is expanded per element into
+// the 2 x 2 real block [[br, bi], [-bi, br]], so the real product's 2N accumulator
+// columns are the interleaved real and imaginary parts of C.
+//
+// FP32 accuracy from TF32 inputs ("3xTF32"): every operand x is split into x_hi =
+// tf32(x) (round to nearest) and x_lo = x - x_hi, and the accumulator takes
+// A_hi B_hi + A_hi B_lo + A_lo B_hi in FP32 (the missing A_lo B_lo term is ~2^-22
+// relative).  The solver's FP64 iterative refinement absorbs the rest.
+//
+// Tiling: one CTA per 128 x 80 complex output tile (M = 128 rows, N = 160 real columns
+// per MMA); K in chunks of 8 complex (16 real) per pipeline stage, 3 stages (two CTAs per SM).  All 256
+// threads stage operands (global -> registers -> split -> shared memory in the
+// K-major, no-swizzle core-matrix layout); thread 0 issues the MMAs for a stage and
+// commits them to that stage's mbarrier, which releases the buffer for reuse.  The
+// accumulator lives in tensor memory (160 of 256 allocated columns) and is read back by
+// the 8 warps (warp w: lanes 32 (w % 4).., columns half (w / 4)).
+// Every wait is bounded: on timeout the kernel records DEV_TIMEOUT in *status, skips
+// the epilogue, frees its tensor memory and returns.
+#include "common.cuh"
+#include "tc_gemm.cuh"
+
+namespace {
+
+constexpr int TC_THREADS = 256;
+constexpr int TM = 128;          // output rows per CTA (UMMA M)
+constexpr int TNC = 80;          // complex output columns per CTA
+constexpr int TNR = 2 * TNC;     // real accumulator columns (UMMA N)
+constexpr int KC = 8;            // complex k per stage
+constexpr int KR = 2 * KC;       // real k per stage
+constexpr int NSTAGE = 3;
+constexpr int TMEM_COLS = 256;
+constexpr uint32_t CORE_BYTES = 128;             // 8 rows x 16 bytes
+constexpr uint32_t LBO = CORE_BYTES;             // next core matrix along K
+constexpr uint32_t SBO = (KR / 4) * CORE_BYTES;  // next 8-row group
+constexpr uint32_t A_BYTES = TM * KR * 4;        // one split of the A tile
+constexpr uint32_t B_BYTES = TNR * KR * 4;       // one split of the B tile
+constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+constexpr size_t SMEM_BYTES = (size_t)NSTAGE * STAGE_BYTES + 1024;
+constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+
+struct TcArgs {
+  int M, N, K;
+  const float2* A;
+  int64_t lda, sA;
+  const float2* B;
+  int64_t ldb, sB;
+  float2* C;
+  int64_t ldc, sC;
+  const float2* C0;
+  int64_t ldc0, sC0;
+  float2 alpha, beta;
+  int32_t* status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// byte offset of real element (r, k) of a K-major no-swizzle tile with KR real k
+__device__ __forceinline__ uint32_t core_off(int r, int k) {
+  return (uint32_t)(r >> 3) * SBO + (uint32_t)(k >> 2) * LBO + (uint32_t)(r & 7) * 16u +
+         (uint32_t)(k & 3) * 4u;
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((LBO >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((SBO >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for tcgen05; no swizzle (layout type 0)
+  return d;
+}
+
+// instruction descriptor: D = F32, A = B = TF32, both K-major, N = TNR, M = TM
+constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TNR >> 3) << 17) |
+                           ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+  uint32_t h;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+  hi = __uint_as_float(h);
+  lo = x - hi;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// true when the phase with the given parity has completed; false after the time limit
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > WAIT_LIMIT_CYCLES) return false;
+  }
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(TC_THREADS, 2) tc_cgemm_kernel(TcArgs p) {
+  extern __shared__ __align__(1024) unsigned char sm_raw[];
+  // stage buffers, then the mbarriers and the tensor-memory address slot
+  unsigned char* stages = sm_raw;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm_raw + (size_t)NSTAGE * STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + NSTAGE);
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t z = blockIdx.z;
+  const float2* A = p.A + z * p.sA;
+  const float2* B = p.B + z * p.sB;
+  const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TNC;
+
+  if (tid == 0) {
+    for (int s = 0; s < NSTAGE; ++s) mbar_init(&mbar[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  const int nkb = (p.K + KC - 1) / KC;
+  // Per-thread operand positions within a stage (independent of the stage):
+  //   A: 4 complex values (rows am[q], k ak[q]);  B: up to 3 (k bk[q], columns bn[q]).
+  int am[4], ak[4], bk[3], bn[3];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (!TA) {
+      const int e = tid * 4 + q;  // 4 consecutive k of one row per thread
+      am[q] = e >> 3;
+      ak[q] = e & 7;
+    } else {
+      const int e = tid + TC_THREADS * q;  // consecutive rows of one k across a warp
+      ak[q] = e >> 7;
+      am[q] = e & 127;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int e = tid + TC_THREADS * q;
+    if (!TB) {
+      bk[q] = e / TNC;
+      bn[q] = e - bk[q] * TNC;
+    } else {
+      bn[q] = e / KC;
+      bk[q] = e - bn[q] * KC;
+    }
+  }
+  auto load_stage = [&](int kb, float2 (&av)[4], float2 (&bv)[3]) {
+    const int k0 = kb * KC;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int gi = i0 + am[q], gk = k0 + ak[q];
+      av[q] = make_float2(0.f, 0.f);
+      if (gi < p.M && gk < p.K)
+        av[q] = TA ? A[(int64_t)gk * p.lda + gi] : A[(int64_t)gi * p.lda + gk];
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int gk = k0 + bk[q], gj = j0 + bn[q];
+      bv[q] = make_float2(0.f, 0.f);
+      if (tid + TC_THREADS * q < KC * TNC && gk < p.K && gj < p.N)
+        bv[q] = TB ? B[(int64_t)gj * p.ldb + gk] : B[(int64_t)gk * p.ldb + gj];
+    }
+  };
+  float2 av[4], bv[3], av_next[4], bv_next[3];
+  if (nkb > 0) load_stage(0, av, bv);
+  bool ok = true;
+  for (int kb = 0; kb < nkb; ++kb) {
+    const int st = kb % NSTAGE;
+    unsigned char* sb = stages + (size_t)st * STAGE_BYTES;
+    // issue the next stage's global loads before anything waits
+    if (kb + 1 < nkb) load_stage(kb + 1, av_next, bv_next);
+    if (kb >= NSTAGE) {
+      // the MMAs that last read this buffer must have completed
+      if (!mbar_wait(&mbar[st], (uint32_t)((kb / NSTAGE - 1) & 1))) ok = false;
+    }
+    if (__syncthreads_or(!ok)) {
+      ok = false;
+      break;
+    }
+    unsigned char* a_hi = sb;
+    unsigned char* a_lo = sb + A_BYTES;
+    unsigned char* b_hi = sb + 2 * A_BYTES;
+    unsigned char* b_lo = sb + 2 * A_BYTES + B_BYTES;
+    // ---- A tile: rows i0 .. i0+127, complex k0 .. k0+7
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float hr, lr, hi_, li;
+      split_tf32(av[q].x, hr, lr);
+      split_tf32(av[q].y, hi_, li);
+      const uint32_t o0 = core_off(am[q], 2 * ak[q]), o1 = o0 + 4u;
+      *reinterpret_cast<float*>(a_hi + o0) = hr;
+      *reinterpret_cast<float*>(a_hi + o1) = hi_;
+      *reinterpret_cast<float*>(a_lo + o0) = lr;
+      *reinterpret_cast<float*>(a_lo + o1) = li;
+    }
+    // ---- B tile: complex k0 .. k0+7, complex columns j0 .. j0+79 (640 complex)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      if (tid + TC_THREADS * q >= KC * TNC) continue;
+      const int kk = bk[q], n = bn[q];
+      float hr, lr, hi_, li;
+      split_tf32(bv[q].x, hr, lr);
+      split_tf32(bv[q].y, hi_, li);
+      // expanded real block [[br, bi], [-bi, br]] at real (k', n') = (2kk.., 2n..),
+      // stored K-major: element (n', k'); 2kk is even, so k' and k'+1 share a core row
+      const uint32_t o00 = core_off(2 * n, 2 * kk), o01 = o00 + 4u;
+      const uint32_t o10 = o00 + 16u, o11 = o10 + 4u;
+      *reinterpret_cast<float*>(b_hi + o00) = hr;
+      *reinterpret_cast<float*>(b_hi + o01) = -hi_;
+      *reinterpret_cast<float*>(b_hi + o10) = hi_;
+      *reinterpret_cast<float*>(b_hi + o11) = hr;
+      *reinterpret_cast<float*>(b_lo + o00) = lr;
+      *reinterpret_cast<float*>(b_lo + o01) = -li;
+      *reinterpret_cast<float*>(b_lo + o10) = li;
+      *reinterpret_cast<float*>(b_lo + o11) = lr;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) av[q] = av_next[q];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) bv[q] = bv_next[q];
+    // make the generic-proxy shared-memory writes visible to the tensor cores
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo);
+      const uint32_t bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+#pragma unroll
+      for (int ks = 0; ks < KR / 8; ++ks) {
+        const uint32_t off = (uint32_t)ks * 2 * LBO;  // 8 real k = two core matrices
+        mma_tf32(tmem, smem_desc(ah + off), smem_desc(bh + off), (kb | ks) ? 1u : 0u);
+        mma_tf32(tmem, smem_desc(ah + off), smem_desc(bl + off), 1u);
+        mma_tf32(tmem, smem_desc(al + off), smem_desc(bh + off), 1u);
+      }
+      mma_commit(&mbar[st]);
+    }
+  }
+  // ---- all MMAs done
+  if (ok && nkb > 0) {
+    const int last = nkb - 1;
+    if (!mbar_wait(&mbar[last % NSTAGE], (uint32_t)((last / NSTAGE) & 1))) ok = false;
+  }
+  ok = !__syncthreads_or(!ok);
+  if (!ok) {
+    if (tid == 0) atomicCAS(p.status, DEV_OK, DEV_TIMEOUT);
+  } else {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int lane_base = 32 * (warp & 3);
+    const int col_half = warp >> 2;  // real columns [80 col_half, 80 col_half + 80)
+    const int row = lane_base + (tid & 31);
+    const int gi = i0 + row;
+    float2* C = p.C + z * p.sC;
+    const float2* C0 = p.C0 ? p.C0 + z * p.sC0 : nullptr;
+#pragma unroll
+    for (int c = 0; c < TNR / 2 / 16; ++c) {
+      const int col = col_half * (TNR / 2) + 16 * c;
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)col, v);
+      if (gi < p.M) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int gj = j0 + col / 2 + q;
+          if (gj < p.N) {
+            float2 acc = make_float2(v[2 * q], v[2 * q + 1]);
+            float2 r = p.alpha * acc;
+            if (C0) r = cfma(p.beta, C0[(int64_t)gi * p.ldc0 + gj], r);
+            C[(int64_t)gi * p.ldc + gj] = r;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_tc_cgemm(int M, int N, int K, bool ta, bool tb, float2 alpha, const float2* A,
+                            int64_t lda, int64_t sA, const float2* B, int64_t ldb, int64_t sB,
+                            float2 beta, const float2* C0, int64_t ldc0, int64_t sC0, float2* C,
+                            int64_t ldc, int64_t sC, int batch, int32_t* status, cudaStream_t s) {
+  if (batch <= 0) return cudaSuccess;
+  if (batch > 65535 || M < 1 || N < 1 || K < 1) return cudaErrorInvalidValue;
+  TcArgs a{M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, C0, ldc0, sC0, alpha, beta, status};
+  dim3 grd((unsigned)ceil_div(N, TNC), (unsigned)ceil_div(M, TM), (unsigned)batch);
+  auto launch = [&](auto kern) -> cudaError_t {
+    RCI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)SMEM_BYTES));
+    kern<<<grd, TC_THREADS, SMEM_BYTES, s>>>(a);
+    rci_note_launch();
+    return cudaGetLastError();
+  };
+  if (!ta && !tb) return launch(tc_cgemm_kernel<false, false>);
+  if (!ta && tb) return launch(tc_cgemm_kernel<false, true>);
+  if (ta && !tb) return launch(tc_cgemm_kernel<true, false>);
+  return launch(tc_cgemm_kernel<true, true>);
+}

@@ -1,0 +1,12 @@
+// Tensor-core (tcgen05, 3xTF32) batched complex FP32 GEMM; see tc_gemm.cu.
+#pragma once
+
+#include "common.cuh"
+
+// C[z] = alpha op(A[z]) op(B[z]) + beta C0[z] for z < batch (row-major complex64,
+// element strides between batch members).  Bounded internal waits: a timeout is
+// recorded as DEV_TIMEOUT in *status.
+cudaError_t launch_tc_cgemm(int M, int N, int K, bool ta, bool tb, float2 alpha, const float2* A,
+                            int64_t lda, int64_t sA, const float2* B, int64_t ldb, int64_t sB,
+                            float2 beta, const float2* C0, int64_t ldc0, int64_t sC0, float2* C,
+                            int64_t ldc, int64_t sC, int batch, int32_t* status, cudaStream_t s);
