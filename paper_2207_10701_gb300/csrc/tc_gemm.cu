@@ -168,50 +168,58 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_cgemm_kernel(TcArgs p) {
   const uint32_t tmem = *tmem_slot;
 
   const int nkb = (p.K + KC - 1) / KC;
-  // Per-thread operand positions within a stage (independent of the stage):
-  //   A: 4 complex values (rows am[q], k ak[q]);  B: up to 3 (k bk[q], columns bn[q]).
-  int am[4], ak[4], bk[3], bn[3];
+  // Work items are pairs of consecutive complex k (= one 16-byte core-matrix row of four
+  // real k), so every shared-memory store is a full 16-byte row.
+  //   A: 128 rows x 4 pairs = 512 items, 2 per thread (row am[q], pair apa[q]);
+  //   B: 80 columns x 4 pairs = 320 items, up to 2 per thread (column bn[r], pair bpb[r]).
+  int am[2], apa[2], bn[2], bpb[2];
+  bool bval[2];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < 2; ++q) {
     if (!TA) {
-      const int e = tid * 4 + q;  // 4 consecutive k of one row per thread
-      am[q] = e >> 3;
-      ak[q] = e & 7;
+      const int e = tid * 2 + q;  // two consecutive pairs (4 consecutive k) of one row
+      am[q] = e >> 2;
+      apa[q] = e & 3;
     } else {
-      const int e = tid + TC_THREADS * q;  // consecutive rows of one k across a warp
-      ak[q] = e >> 7;
-      am[q] = e & 127;
+      const int e = tid + TC_THREADS * q;  // consecutive rows across a warp
+      am[q] = e & (TM - 1);
+      apa[q] = e >> 7;
     }
   }
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    const int e = tid + TC_THREADS * q;
+  for (int r = 0; r < 2; ++r) {
+    const int e = tid + TC_THREADS * r;
+    bval[r] = e < TNC * (KC / 2);
     if (!TB) {
-      bk[q] = e / TNC;
-      bn[q] = e - bk[q] * TNC;
+      bn[r] = e % TNC;  // consecutive columns across a warp
+      bpb[r] = e / TNC;
     } else {
-      bn[q] = e / KC;
-      bk[q] = e - bn[q] * KC;
+      bpb[r] = e & 3;  // consecutive k pairs of one column
+      bn[r] = e >> 2;
     }
   }
-  auto load_stage = [&](int kb, float2 (&av)[4], float2 (&bv)[3]) {
+  auto load_stage = [&](int kb, float2 (&av)[2][2], float2 (&bv)[2][2]) {
     const int k0 = kb * KC;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int gi = i0 + am[q], gk = k0 + ak[q];
-      av[q] = make_float2(0.f, 0.f);
-      if (gi < p.M && gk < p.K)
-        av[q] = TA ? A[(int64_t)gk * p.lda + gi] : A[(int64_t)gi * p.lda + gk];
-    }
+    for (int q = 0; q < 2; ++q)
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const int gk = k0 + bk[q], gj = j0 + bn[q];
-      bv[q] = make_float2(0.f, 0.f);
-      if (tid + TC_THREADS * q < KC * TNC && gk < p.K && gj < p.N)
-        bv[q] = TB ? B[(int64_t)gj * p.ldb + gk] : B[(int64_t)gk * p.ldb + gj];
-    }
+      for (int c = 0; c < 2; ++c) {
+        const int gi = i0 + am[q], gk = k0 + 2 * apa[q] + c;
+        av[q][c] = make_float2(0.f, 0.f);
+        if (gi < p.M && gk < p.K)
+          av[q][c] = TA ? A[(int64_t)gk * p.lda + gi] : A[(int64_t)gi * p.lda + gk];
+      }
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int gk = k0 + 2 * bpb[r] + c, gj = j0 + bn[r];
+        bv[r][c] = make_float2(0.f, 0.f);
+        if (bval[r] && gk < p.K && gj < p.N)
+          bv[r][c] = TB ? B[(int64_t)gj * p.ldb + gk] : B[(int64_t)gk * p.ldb + gj];
+      }
   };
-  float2 av[4], bv[3], av_next[4], bv_next[3];
+  float2 av[2][2], bv[2][2], av_next[2][2], bv_next[2][2];
   if (nkb > 0) load_stage(0, av, bv);
   bool ok = true;
   for (int kb = 0; kb < nkb; ++kb) {
@@ -231,43 +239,42 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_cgemm_kernel(TcArgs p) {
     unsigned char* a_lo = sb + A_BYTES;
     unsigned char* b_hi = sb + 2 * A_BYTES;
     unsigned char* b_lo = sb + 2 * A_BYTES + B_BYTES;
-    // ---- A tile: rows i0 .. i0+127, complex k0 .. k0+7
+    // ---- A tile: rows i0 .. i0+127, complex k0 .. k0+7: row am, real k 4 apa .. 4 apa + 3
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float hr, lr, hi_, li;
-      split_tf32(av[q].x, hr, lr);
-      split_tf32(av[q].y, hi_, li);
-      const uint32_t o0 = core_off(am[q], 2 * ak[q]), o1 = o0 + 4u;
-      *reinterpret_cast<float*>(a_hi + o0) = hr;
-      *reinterpret_cast<float*>(a_hi + o1) = hi_;
-      *reinterpret_cast<float*>(a_lo + o0) = lr;
-      *reinterpret_cast<float*>(a_lo + o1) = li;
+    for (int q = 0; q < 2; ++q) {
+      float h[4], l[4];
+      split_tf32(av[q][0].x, h[0], l[0]);
+      split_tf32(av[q][0].y, h[1], l[1]);
+      split_tf32(av[q][1].x, h[2], l[2]);
+      split_tf32(av[q][1].y, h[3], l[3]);
+      const uint32_t o = core_off(am[q], 4 * apa[q]);
+      *reinterpret_cast<float4*>(a_hi + o) = make_float4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4*>(a_lo + o) = make_float4(l[0], l[1], l[2], l[3]);
     }
-    // ---- B tile: complex k0 .. k0+7, complex columns j0 .. j0+79 (640 complex)
+    // ---- B tile: complex k0 .. k0+7, complex columns j0 .. j0+79.  Each complex b
+    // expands into the real block [[br, bi], [-bi, br]] at (k', n') = (2k.., 2n..), stored
+    // K-major (element (n', k')): row 2n gets (br, -bi), row 2n+1 gets (bi, br) per k.
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      if (tid + TC_THREADS * q >= KC * TNC) continue;
-      const int kk = bk[q], n = bn[q];
-      float hr, lr, hi_, li;
-      split_tf32(bv[q].x, hr, lr);
-      split_tf32(bv[q].y, hi_, li);
-      // expanded real block [[br, bi], [-bi, br]] at real (k', n') = (2kk.., 2n..),
-      // stored K-major: element (n', k'); 2kk is even, so k' and k'+1 share a core row
-      const uint32_t o00 = core_off(2 * n, 2 * kk), o01 = o00 + 4u;
-      const uint32_t o10 = o00 + 16u, o11 = o10 + 4u;
-      *reinterpret_cast<float*>(b_hi + o00) = hr;
-      *reinterpret_cast<float*>(b_hi + o01) = -hi_;
-      *reinterpret_cast<float*>(b_hi + o10) = hi_;
-      *reinterpret_cast<float*>(b_hi + o11) = hr;
-      *reinterpret_cast<float*>(b_lo + o00) = lr;
-      *reinterpret_cast<float*>(b_lo + o01) = -li;
-      *reinterpret_cast<float*>(b_lo + o10) = li;
-      *reinterpret_cast<float*>(b_lo + o11) = lr;
+    for (int r = 0; r < 2; ++r) {
+      if (!bval[r]) continue;
+      float rh0, rl0, ih0, il0, rh1, rl1, ih1, il1;
+      split_tf32(bv[r][0].x, rh0, rl0);
+      split_tf32(bv[r][0].y, ih0, il0);
+      split_tf32(bv[r][1].x, rh1, rl1);
+      split_tf32(bv[r][1].y, ih1, il1);
+      const uint32_t o = core_off(2 * bn[r], 4 * bpb[r]);
+      *reinterpret_cast<float4*>(b_hi + o) = make_float4(rh0, -ih0, rh1, -ih1);
+      *reinterpret_cast<float4*>(b_hi + o + 16u) = make_float4(ih0, rh0, ih1, rh1);
+      *reinterpret_cast<float4*>(b_lo + o) = make_float4(rl0, -il0, rl1, -il1);
+      *reinterpret_cast<float4*>(b_lo + o + 16u) = make_float4(il0, rl0, il1, rl1);
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) av[q] = av_next[q];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) bv[q] = bv_next[q];
+    for (int q = 0; q < 2; ++q) {
+      av[q][0] = av_next[q][0];
+      av[q][1] = av_next[q][1];
+      bv[q][0] = bv_next[q][0];
+      bv[q][1] = bv_next[q][1];
+    }
     // make the generic-proxy shared-memory writes visible to the tensor cores
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();

@@ -271,3 +271,64 @@ def test_repeat_is_bitwise_deterministic():
     g.factor()
     F2, _ = g.avg_intensity(wl.objective, wl.light)
     assert F1 == F2
+
+
+def test_concurrent_evaluations_match_alone():
+    # the same designs evaluated alone and as an overlapping mix on three streams
+    # (one host thread per evaluator) give bitwise the same results
+    import threading
+    wl = CASES["small_plane"]()
+    designs = [_widths(wl, s) for s in range(9)]
+    with P.Grid(wl.grid, prec=P.FP32_REFINE) as g:
+        alone = []
+        for ws in designs:
+            g.set_design(ws)
+            g.factor()
+            alone.append(g.avg_intensity(wl.objective, wl.light)[0])
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    grids = [P.Grid(wl.grid, prec=P.FP32_REFINE, stream=s) for s in streams]
+    mixed = [None] * len(designs)
+
+    def worker(w):
+        for k in range(w, len(designs), 3):
+            grids[w].set_design(designs[k])
+            grids[w].factor()
+            mixed[k] = grids[w].avg_intensity(wl.objective, wl.light)[0]
+
+    ths = [threading.Thread(target=worker, args=(w,)) for w in range(3)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    for gr in grids:
+        gr.close()
+    assert mixed == alone
+
+
+@pytest.mark.parametrize("maker", [W.c3_precision, W.c4_gradient])
+def test_full_size_virtual_focus_properties(maker):
+    # Full-size grids (C3: 20040 x 224, 4.5M unknowns) are too large for an oracle solve
+    # in a test, so the oracle checks what it can compute independently: its own
+    # virtual-focus right-hand side, the FP64 stencil residual of the GPU field against
+    # it, and its own quadratic form of the GPU's source-plane field.
+    from oracle.grid import objective_vector
+    from oracle.reciprocal import qform_direct
+    wl = maker()
+    og = OGrid(wl.grid)
+    ws = W.widths(wl.grid.n_cells, 21)
+    with P.Grid(wl.grid, prec=P.FP32_REFINE) as g:
+        g.set_design(ws)
+        g.factor()
+        F, info = g.avg_intensity(wl.objective, wl.light)
+        v_src, v_full, _ = g.solve_reciprocal(wl.objective, full=True)
+        v_src = _cplx(v_src)
+        z = np.conj(_cplx(v_full)).reshape(og.nx, og.ny)
+    assert info.rel_residual <= 1e-10
+    b = np.conj(objective_vector(og, wl.objective))
+    coeffs = stencil_coefficients(og, rasterize_eps(og, ws))
+    r = b - apply_A(og, coeffs, z)
+    assert np.linalg.norm(r) <= 1e-9 * np.linalg.norm(b)
+    lags = W_lags(wl.light, og.k_sub, og.h, og.n_src)
+    F_ref = qform_direct(v_src, lags)
+    assert abs(F - F_ref) <= 1e-10 * abs(F_ref)
+    assert F > 0
