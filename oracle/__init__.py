@@ -18,6 +18,8 @@ Modules
               Sec. 5.1, in the exact reading), Gauss-Legendre rules (Sec. 5.2).
   reciprocal  reciprocal average v^dag W v (Eq. 7), brute-force angle average (Eq. 6),
               FFT and spectral forms of the quadratic form.
+  gradient    dF/d(widths) by the adjoint of v^dag W v (Sec. 4.1), the brute-force
+              gradient of Eq. 6 angle by angle, and the derivative of the fill raster.
 
 Every function is pinned by a ``-m "not gpu"`` test against something other than
 itself (closed forms, library routines used as independent checks, invariants, the
