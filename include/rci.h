@@ -183,6 +183,21 @@ rci_status rci_solve_reciprocal(rci_grid* g, const rci_objective* obj, double* v
 rci_status rci_avg_intensity(rci_grid* g, const rci_objective* obj, const rci_light* light,
                              double* out, rci_info* info);
 
+/* Averaged figure of merit and its gradient with respect to the pillar widths, by
+ * the adjoint of Eq. 7 (Sec. 4.1: dF = 2 Re(v^dag W dv), and dv costs one more solve
+ * with the same factorisation).  With z = A^{-1} conj(w), v = conj(z) on S, g = W v:
+ *   mu = A^{-1} P_S^T g   (second refined solve; A = A^T),
+ *   dF/dw_m = -2 Re sum_c mu_c z_c k0^2 s_x s_y d(eps_c)/d(w_m),
+ * where, in the pillar rows, d(eps_c)/d(w_m) = (eps_pillar - eps_air)/(2h) for each
+ * column holding an edge of pillar m (the raster's area fill is piecewise linear in
+ * the width).  At a tie (edge exactly on a column boundary) the derivative for a
+ * growing width is taken.  value: HOST double (the same number rci_avg_intensity
+ * returns).  dF_dwidths: HOST float64[n_cells].  Either may be NULL.
+ * Errors: as rci_avg_intensity; ENOCONV if either solve ends above the tolerance
+ * (outputs still written). */
+rci_status rci_avg_intensity_grad(rci_grid* g, const rci_objective* obj, const rci_light* light,
+                                  double* value, double* dF_dwidths, rci_info* info);
+
 /* Brute-force average of Eq. 6 on the same factorisation: for each angle theta_q
  * (measured in the substrate) the equivalent current b0 = sqrt(cos theta) exp(i k_s
  * sin(theta) x_i) on row j_src over S, u_q = A^{-1} b0, f_q = |w^dag u_q|^2, and
@@ -239,7 +254,8 @@ rci_status rci_apply_operator(rci_grid* g, const double* x, double* y);
  * Kernel families timed by the profiler:
  *   0 level-0 tridiagonal factor and first Schur blocks, 1 block inversions,
  *   2 factorisation GEMMs, 3 forward/backward substitution, 4 FP64 stencil residual,
- *   5 quadratic form, 6 raster/assembly/right-hand sides. */
+ *   5 quadratic form, 6 raster/assembly/right-hand sides, 7 gradient (W v product and
+ *   width chain rule; its solve counts under 3 and 4). */
 #define RCI_PROFILE_FAMILIES 8
 typedef struct {
   double ms[RCI_PROFILE_FAMILIES];      /* device time (CUDA events on the grid's stream) */

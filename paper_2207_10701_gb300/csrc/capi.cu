@@ -49,6 +49,9 @@ struct rci_grid {
   void *m32a = nullptr, *m32b = nullptr;
   double *th_d = nullptr, *wq_d = nullptr, *f_d = nullptr;
   int th_cap = 0;
+  // gradient buffers (allocated by the first gradient call)
+  double2 *mu = nullptr, *gsrc = nullptr, *tpart = nullptr;
+  double* dgrad = nullptr;
   // light cache
   bool lags_valid = false;
   rci_light lags_key{};
@@ -444,7 +447,7 @@ rci_status rci_destroy_grid(rci_grid* g) {
   void* ps[] = {g->widths, g->eps, g->dg, g->cx, g->cy, g->dg0, g->kss, g->b1, g->x1, g->r1, g->r32, g->d32,
                 g->crow, g->vsrc, g->lags, g->qpart, g->dscal, g->part_r, g->part_b, g->ratio,
                 g->vf_scratch, g->dstatus, g->mb, g->mx, g->mr, g->m32a, g->m32b, g->th_d,
-                g->wq_d, g->f_d};
+                g->wq_d, g->f_d, g->mu, g->gsrc, g->tpart, g->dgrad};
   for (void* p : ps) dfree(p);
   bcr_destroy(g->bcr);
   if (g->prof.pool) {
@@ -658,6 +661,76 @@ rci_status rci_avg_intensity(rci_grid* g, const rci_objective* obj, const rci_li
     info->ms_factor = ms;
   }
   return sst;
+}
+
+rci_status rci_avg_intensity_grad(rci_grid* g, const rci_objective* obj, const rci_light* light,
+                                  double* value, double* dF_dwidths, rci_info* info) {
+  if (!g) return RCI_EINVAL;
+  DeviceGuard dg(g->device);
+  rci_status st = check_light(g, light);
+  if (st != RCI_OK) return st;
+  const GridGeom& G = g->g;
+  const int64_t ns = G.n_src;
+  if (!g->mu) {
+    CK(dalloc(g, &g->mu, sizeof(double2) * g->N), "gradient buffers");
+    CK(dalloc(g, &g->gsrc, sizeof(double2) * ns), "gradient buffers");
+    CK(dalloc(g, &g->tpart, sizeof(double2) * ns * toeplitz_mv_chunks(ns)), "gradient buffers");
+    CK(dalloc(g, &g->dgrad, sizeof(double) * g->d.n_cells), "gradient buffers");
+  }
+  // forward: z = A^{-1} conj(w) in x1, v on the source plane, F = v^dag W v
+  rci_info i1{};
+  rci_status s1 = reciprocal_solve(g, obj, &i1);
+  if (s1 != RCI_OK && s1 != RCI_ENOCONV) return s1;
+  st = ensure_lags(g, light);
+  if (st != RCI_OK) return st;
+  {
+    const double n = (double)ns;
+    ProfScope ps(&g->prof, PF_QFORM, g->s, 2.0 * n * n, 24.0 * n, 2);
+    CK(launch_qform(g->vsrc, g->lags, ns, g->qpart, g->dscal, g->s), "qform");
+  }
+  // adjoint right-hand side P_S^T (W v) and mu = A^{-1} P_S^T (W v)
+  {
+    const double n = (double)ns;
+    ProfScope ps(&g->prof, PF_GRAD, g->s, 4.0 * n * n, 40.0 * n, 2);
+    CK(launch_toeplitz_mv(g->vsrc, g->lags, ns, g->tpart, g->gsrc, g->s), "W v");
+  }
+  CK(cudaMemsetAsync(g->b1, 0, sizeof(double2) * g->N, g->s), "zero rhs");
+  CK(launch_scatter_row(G, g->gsrc, G.j_src, g->b1, g->s), "adjoint rhs");
+  rci_info i2{};
+  CK(cudaEventRecord(g->ev[2], g->s), "event");
+  rci_status s2 = refined_solve(g, g->b1, g->mu, g->r1, g->r32, g->d32, 1, &i2);
+  CK(cudaEventRecord(g->ev[3], g->s), "event");
+  if (s2 != RCI_OK && s2 != RCI_ENOCONV) return s2;
+  {
+    const double rows = (double)(G.j_p1 - G.j_p0);
+    ProfScope ps(&g->prof, PF_GRAD, g->s, 2.0 * 20.0 * rows * g->d.n_cells,
+                 2.0 * 48.0 * rows * g->d.n_cells, 1);
+    CK(launch_width_grad(G, g->widths, g->mu, g->x1, g->kss, g->dgrad, g->s), "width gradient");
+  }
+  double F = 0.0;
+  CK(cudaMemcpyAsync(&F, g->dscal, sizeof(double), cudaMemcpyDeviceToHost, g->s), "qform copy");
+  std::vector<double> grad(dF_dwidths ? g->d.n_cells : 0);
+  if (dF_dwidths)
+    CK(cudaMemcpyAsync(grad.data(), g->dgrad, sizeof(double) * g->d.n_cells,
+                       cudaMemcpyDeviceToHost, g->s),
+       "gradient copy");
+  CK(cudaStreamSynchronize(g->s), "gradient");
+  if (g->prof.on) g->prof.collect();
+  if (!std::isfinite(F)) return fail(g, RCI_ENUMERIC, "non-finite averaged intensity");
+  for (double x : grad)
+    if (!std::isfinite(x)) return fail(g, RCI_ENUMERIC, "non-finite gradient");
+  if (value) *value = F;
+  if (dF_dwidths) std::memcpy(dF_dwidths, grad.data(), sizeof(double) * grad.size());
+  if (info) {
+    info->refine_iters = i1.refine_iters > i2.refine_iters ? i1.refine_iters : i2.refine_iters;
+    info->rel_residual = i1.rel_residual > i2.rel_residual ? i1.rel_residual : i2.rel_residual;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, g->ev[2], g->ev[3]);
+    info->ms_solve = i1.ms_solve + ms;
+    cudaEventElapsedTime(&ms, g->ev[0], g->ev[1]);
+    info->ms_factor = ms;
+  }
+  return s1 != RCI_OK ? s1 : s2;
 }
 
 rci_status rci_solve_angles(rci_grid* g, const rci_objective* obj, const double* theta,

@@ -86,7 +86,8 @@ enum ProfFamily : int {
   PF_RESIDUAL = 4, // FP64 stencil residual + norms
   PF_QFORM = 5,    // Toeplitz quadratic form
   PF_SETUP = 6,    // raster, assembly, right-hand sides, conversions
-  PF_COUNT = 7
+  PF_GRAD = 7,     // Toeplitz product W v and the width chain rule of the gradient
+  PF_COUNT = 8
 };
 
 struct Profiler {

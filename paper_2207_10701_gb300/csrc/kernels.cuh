@@ -70,6 +70,16 @@ cudaError_t launch_w_lags(int kind, double c, double th1, double th2, double k_s
 cudaError_t launch_weighted_sum(const double* w, const double* f, int nq, double* out,
                                 cudaStream_t s);
 
+// grad.cu
+// g = W v for the real symmetric Toeplitz W (lags[0..n-1]); part holds
+// toeplitz_mv_chunks(n) * n complex partials
+int64_t toeplitz_mv_chunks(int64_t n);
+cudaError_t launch_toeplitz_mv(const double2* v, const double* lags, int64_t n, double2* part,
+                               double2* out, cudaStream_t s);
+// out[m] = dF/dw_m = -2 Re sum_c mu_c z_c kss_c d eps_c/d w_m (pillar rows, edge columns)
+cudaError_t launch_width_grad(const GridGeom& g, const double* widths, const double2* mu,
+                              const double2* z, const double2* kss, double* out, cudaStream_t s);
+
 // qform.cu
 int64_t qform_num_partials(int64_t n);
 cudaError_t launch_qform(const double2* v, const double* lags, int64_t n, double* partials,

@@ -45,7 +45,7 @@ class InfoC(C.Structure):
                 ("ms_solve", C.c_double), ("ms_qform", C.c_double)]
 
 
-PROFILE_FAMILIES = ["level0", "invert", "gemm", "solve", "residual", "qform", "setup", "spare"]
+PROFILE_FAMILIES = ["level0", "invert", "gemm", "solve", "residual", "qform", "setup", "grad"]
 
 
 class ProfileC(C.Structure):
@@ -86,6 +86,8 @@ EXPORTED = {
     "rci_solve_reciprocal": (C.c_int, [_P, C.POINTER(ObjectiveC), _P, _P, C.POINTER(InfoC)]),
     "rci_avg_intensity": (C.c_int, [_P, C.POINTER(ObjectiveC), C.POINTER(LightC), _D,
                                     C.POINTER(InfoC)]),
+    "rci_avg_intensity_grad": (C.c_int, [_P, C.POINTER(ObjectiveC), C.POINTER(LightC), _D, _D,
+                                         C.POINTER(InfoC)]),
     "rci_solve_angles": (C.c_int, [_P, C.POINTER(ObjectiveC), _D, _D, C.c_int64, _D, _D,
                                    C.POINTER(InfoC)]),
     "rci_avg_bruteforce": (C.c_int, [_P, C.POINTER(ObjectiveC), C.POINTER(LightC), C.c_int64,
@@ -190,6 +192,7 @@ class Grid:
         _check(lib().rci_grid_query(h, C.byref(nx), C.byref(ny), C.byref(ns), C.byref(by)), h)
         self.nx, self.ny, self.n_src = nx.value, ny.value, ns.value
         self.N = self.nx * self.ny
+        self.n_cells = int(desc.n_cells)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -217,7 +220,7 @@ class Grid:
         p = ProfileC()
         _check(lib().rci_profile_read(self._h, C.byref(p)), self._h)
         return {f: {"ms": p.ms[i], "flops": p.flops[i], "bytes": p.bytes[i],
-                    "launches": p.launches[i]} for i, f in enumerate(PROFILE_FAMILIES[:7])}
+                    "launches": p.launches[i]} for i, f in enumerate(PROFILE_FAMILIES)}
 
     def device_bytes(self) -> int:
         by = C.c_size_t()
@@ -267,6 +270,18 @@ class Grid:
         _check(lib().rci_avg_intensity(self._h, C.byref(oc), C.byref(lc), C.byref(out),
                                        C.byref(info)), self._h)
         return out.value, Info.of(info)
+
+    def avg_intensity_grad(self, obj, light):
+        """(F, dF/d widths as float64[n_cells], Info): the adjoint gradient of Eq. 7
+        (one extra refined solve on the same factorisation)."""
+        keep = []
+        oc, lc = _objective(obj, keep), _light(light, keep)
+        out = C.c_double()
+        grad = np.empty(self.n_cells)
+        info = InfoC()
+        _check(lib().rci_avg_intensity_grad(self._h, C.byref(oc), C.byref(lc), C.byref(out),
+                                            _hptr(grad), C.byref(info)), self._h)
+        return out.value, grad, Info.of(info)
 
     def solve_angles(self, obj, theta, weight):
         keep = []
