@@ -455,6 +455,237 @@ gj_inverse_kernel(cplx<T>* __restrict__ src, int64_t src_stride, cplx<T>* __rest
     for (int j = tid; j < n; j += NT) o[i * n + j] = a[i * n + idx[j]];
 }
 
+// Register-panel variant: the panel is NB = NT/32 columns wide and warp t holds panel
+// column t in registers (lane L keeps rows L, L+32, ..., R slots).  A pivot step then
+// costs one block barrier: after its own update, the warp that holds the next pivot
+// column searches it (shuffles), publishes the swapped column, the pivot row index and
+// 1/pivot to a double-buffered shared slot, and every warp updates its column from that
+// slot and from shuffles of its own registers (rows k and p).  The update of the other
+// columns after each panel is the one of gj_inverse_kernel.
+template <typename T, int R>
+__device__ __forceinline__ cplx<T> reg_select(const cplx<T> (&x)[R], int s) {
+  cplx<T> v = x[0];
+#pragma unroll
+  for (int r = 1; r < R; ++r)
+    if (s == r) v = x[r];
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ cplx<T> shfl_c(cplx<T> v, int src) {
+  return mkc(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// value held for row `row` by the warp (row = slot * 32 + lane)
+template <typename T, int R>
+__device__ __forceinline__ cplx<T> warp_row(const cplx<T> (&x)[R], int row) {
+  return shfl_c<T>(reg_select<T, R>(x, row >> 5), row & 31);
+}
+
+// Pivot search on the warp's column (rows k..n-1), ties to the lowest row; publishes the
+// column after the swap of rows k and p, p and 1/pivot.  Returns false if singular.
+template <typename T, int R>
+__device__ __forceinline__ bool gj_pivot(const cplx<T> (&x)[R], int k, int n, int lane,
+                                         cplx<T>* colk, int* s_p, cplx<T>* s_pinv, int* perm) {
+  T best = T(-1);
+  int bi = k;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = lane + 32 * r;
+    if (i >= k && i < n) {
+      T v = cabs1(x[r]);
+      if (v > best) {
+        best = v;
+        bi = i;
+      }
+    }
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    T ob = __shfl_xor_sync(0xffffffffu, best, off);
+    int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+    if (ob > best || (ob == best && oi < bi)) {
+      best = ob;
+      bi = oi;
+    }
+  }
+  const int p = bi;
+  const cplx<T> vp = warp_row<T, R>(x, p), vk = warp_row<T, R>(x, k);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = lane + 32 * r;
+    if (i < n) colk[i] = i == k ? vp : (i == p ? vk : x[r]);
+  }
+  if (lane == 0) {
+    *s_p = p;
+    *s_pinv = crecip(vp);
+    perm[k] = p;
+  }
+  return best > T(0);
+}
+
+template <typename T, bool SMEM, int R, int TR, int TC, int NT>
+__global__ void __launch_bounds__(NT)
+gj_regpanel_kernel(cplx<T>* __restrict__ src, int64_t src_stride, cplx<T>* __restrict__ out,
+                   int64_t out_stride, int n, int32_t* status) {
+  constexpr int NB = NT / 32;
+  constexpr int TY = NT / 32;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const GjSmem<T> L(n, NB, SMEM);
+  cplx<T>* const cbuf0 = reinterpret_cast<cplx<T>*>(sm_raw + L.coln);  // published pivot
+  cplx<T>* const cbuf1 = reinterpret_cast<cplx<T>*>(sm_raw + L.colk);  // columns, alternating
+  cplx<T>* tp = reinterpret_cast<cplx<T>*>(sm_raw + L.tpanel);
+  int* perm = reinterpret_cast<int*>(sm_raw + L.perm);
+  int* idx = reinterpret_cast<int*>(sm_raw + L.idx);
+  __shared__ int s_p[2];
+  __shared__ cplx<T> s_pinv[2];
+  __shared__ int s_sing;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  cplx<T>* g = src + (int64_t)blockIdx.x * src_stride;
+  cplx<T>* a = SMEM ? reinterpret_cast<cplx<T>*>(sm_raw + L.mat) : g;
+  if (tid == 0) s_sing = 0;
+  if (SMEM) {
+    for (int e = tid; e < n * n; e += NT) a[e] = g[e];
+  }
+  for (int c0 = 0; c0 < n; c0 += NB) {
+    const int nb = n - c0 < NB ? n - c0 : NB;
+    const int t = warp, j = c0 + t;
+    __syncthreads();
+    cplx<T> x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i = lane + 32 * r;
+      x[r] = (t < nb && i < n) ? a[i * n + j] : czero<T>();
+    }
+    if (warp == 0 && !gj_pivot<T, R>(x, c0, n, lane, cbuf0, &s_p[0], &s_pinv[0], perm))
+      s_sing = 1;
+    __syncthreads();
+    // ---------------- panel: one barrier per pivot
+    for (int kt = 0; kt < nb; ++kt) {
+      const int k = c0 + kt, b = kt & 1;
+      if (t < nb) {
+        const int p = s_p[b];
+        const cplx<T> pinv = s_pinv[b];
+        const cplx<T>* colk = b ? cbuf1 : cbuf0;
+        const cplx<T> vp = warp_row<T, R>(x, p), vk = warp_row<T, R>(x, k);
+        const cplx<T> rk = (t == kt ? mkc(T(1), T(0)) : vp) * pinv;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int i = lane + 32 * r;
+          if (i < n) {
+            const cplx<T> old = i == k ? vp : (i == p ? vk : x[r]);
+            const cplx<T> base = t == kt ? czero<T>() : old;
+            x[r] = i == k ? rk : cfms(colk[i], rk, base);
+          }
+        }
+        if (t == kt + 1 &&
+            !gj_pivot<T, R>(x, k + 1, n, lane, b ? cbuf0 : cbuf1, &s_p[b ^ 1], &s_pinv[b ^ 1],
+                            perm))
+          s_sing = 1;
+      }
+      __syncthreads();
+    }
+    if (t < nb) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int i = lane + 32 * r;
+        if (i < n) a[i * n + j] = x[r];
+      }
+    }
+    const int m = n - nb;
+    if (m == 0) continue;
+    // ---------------- panel row swaps on the other columns, in order; stage panel rows
+    for (int jj = tid; jj < m; jj += NT) {
+      const int jc = jj < c0 ? jj : jj + nb;
+      for (int u = 0; u < nb; ++u) {
+        const int rr = c0 + u, p = perm[rr];
+        if (p != rr) {
+          cplx<T> y = a[rr * n + jc];
+          a[rr * n + jc] = a[p * n + jc];
+          a[p * n + jc] = y;
+        }
+      }
+    }
+    __syncthreads();
+    for (int u = 0; u < nb; ++u)
+      for (int jj = tid; jj < m; jj += NT) {
+        const int jc = jj < c0 ? jj : jj + nb;
+        tp[u * m + jj] = a[(c0 + u) * n + jc];
+      }
+    __syncthreads();
+    // ---------------- other columns (register tiles TR x TC)
+    const int ty = warp, tx = lane;
+    for (int r0 = 0; r0 < n; r0 += TY * TR) {
+      for (int q0 = 0; q0 < m; q0 += 32 * TC) {
+        cplx<T> acc[TR][TC];
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+          for (int c = 0; c < TC; ++c) {
+            const int i = r0 + ty + TY * r, jj = q0 + tx + 32 * c;
+            const int jc = jj < c0 ? jj : jj + nb;
+            const bool panel_row = i >= c0 && i < c0 + nb;
+            acc[r][c] = (i < n && jj < m && !panel_row) ? a[i * n + jc] : czero<T>();
+          }
+        for (int u = 0; u < nb; ++u) {
+          cplx<T> zv[TR], tv[TC];
+#pragma unroll
+          for (int r = 0; r < TR; ++r) {
+            const int i = r0 + ty + TY * r;
+            zv[r] = i < n ? a[i * n + c0 + u] : czero<T>();
+          }
+#pragma unroll
+          for (int c = 0; c < TC; ++c) {
+            const int jj = q0 + tx + 32 * c;
+            tv[c] = jj < m ? tp[u * m + jj] : czero<T>();
+          }
+#pragma unroll
+          for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int c = 0; c < TC; ++c) acc[r][c] = cfma(zv[r], tv[c], acc[r][c]);
+        }
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+          for (int c = 0; c < TC; ++c) {
+            const int i = r0 + ty + TY * r, jj = q0 + tx + 32 * c;
+            const int jc = jj < c0 ? jj : jj + nb;
+            if (i < n && jj < m) a[i * n + jc] = acc[r][c];
+          }
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int jx = 0; jx < n; ++jx) idx[jx] = jx;
+    for (int k = n - 1; k >= 0; --k) {
+      int p = perm[k];
+      int y = idx[k];
+      idx[k] = idx[p];
+      idx[p] = y;
+    }
+    if (s_sing) atomicCAS(status, DEV_OK, DEV_SINGULAR);
+  }
+  __syncthreads();
+  cplx<T>* o = out + (int64_t)blockIdx.x * out_stride;
+  for (int i = 0; i < n; ++i)
+    for (int jx = tid; jx < n; jx += NT) o[i * n + jx] = a[i * n + idx[jx]];
+}
+
+template <typename T, bool SMEM, int R, int TR, int TC, int NT>
+cudaError_t launch_gj_reg(cplx<T>* src, int64_t src_stride, cplx<T>* out, int64_t out_stride,
+                          int n, int batch, int32_t* status, cudaStream_t s) {
+  const GjSmem<T> L(n, NT / 32, SMEM);
+  if (L.total > SMEM_LIMIT || n > 32 * R) return cudaErrorInvalidValue;
+  if (L.total > 48 * 1024)
+    RCI_CUDA_TRY(cudaFuncSetAttribute(gj_regpanel_kernel<T, SMEM, R, TR, TC, NT>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+  gj_regpanel_kernel<T, SMEM, R, TR, TC, NT><<<batch, NT, L.total, s>>>(src, src_stride, out,
+                                                                        out_stride, n, status);
+  rci_note_launch();
+  return cudaGetLastError();
+}
+
 template <typename T, bool SMEM, int NB, int TR, int TC, int NT>
 cudaError_t launch_gj_cfg(cplx<T>* src, int64_t src_stride, cplx<T>* out, int64_t out_stride,
                           int n, int batch, int32_t* status, cudaStream_t s) {
@@ -475,14 +706,20 @@ cudaError_t launch_gj(cplx<T>* src, int64_t src_stride, cplx<T>* out, int64_t ou
   if (batch <= 0) return cudaSuccess;
   if (n > 1024) return cudaErrorInvalidValue;
   if constexpr (sizeof(T) == 4) {
-    if (GjSmem<T>(n, 16, true).total <= SMEM_LIMIT)
-      return launch_gj_cfg<T, true, 16, 5, 5, 512>(src, src_stride, out, out_stride, n, batch,
+    if (n <= 160 && GjSmem<T>(n, 16, true).total <= SMEM_LIMIT)
+      return launch_gj_reg<T, true, 5, 5, 5, 512>(src, src_stride, out, out_stride, n, batch,
+                                                  status, s);
+    if (n <= 256)
+      return launch_gj_reg<T, false, 8, 5, 5, 512>(src, src_stride, out, out_stride, n, batch,
                                                    status, s);
     return launch_gj_cfg<T, false, 16, 5, 5, 512>(src, src_stride, out, out_stride, n, batch,
                                                   status, s);
   } else {
-    if (GjSmem<T>(n, 16, true).total <= SMEM_LIMIT)
-      return launch_gj_cfg<T, true, 16, 5, 5, 256>(src, src_stride, out, out_stride, n, batch,
+    if (n <= 160 && GjSmem<T>(n, 8, true).total <= SMEM_LIMIT)
+      return launch_gj_reg<T, true, 5, 5, 5, 256>(src, src_stride, out, out_stride, n, batch,
+                                                  status, s);
+    if (n <= 256)
+      return launch_gj_reg<T, false, 8, 5, 5, 256>(src, src_stride, out, out_stride, n, batch,
                                                    status, s);
     if (GjSmem<T>(n, 16, false).total <= SMEM_LIMIT)
       return launch_gj_cfg<T, false, 16, 5, 5, 256>(src, src_stride, out, out_stride, n, batch,
