@@ -128,11 +128,30 @@ def _max_over_ranks(x: float, ws: int) -> float:
     return float(t.item())
 
 
-def _roofline(fam: str, stats: dict, prec: int, peaks: dict, peak_kind: str):
+# DRAM bytes (read + write) per ny x ny block inverted by the FP32 register-panel Gauss-Jordan
+# kernel, from one ncu capture of its 1010-block launch in the 200-wavelength factorisation
+# (207.7 MB read + 155.9 MB written; the kernel reads each block once and writes its inverse
+# once, 409.6 KB algorithmic).  Only valid for ny = 160 and that kernel as it stands.
+GJ_FP32_DRAM_BYTES_PER_BLOCK_NY160 = (207.685e6 + 155.907e6) / 1010
+# nominal dense TF32 / BF16 tensor rate (1.1 / 2.25 PFLOP/s)
+TF32_OVER_BF16 = 1.1 / 2.25
+
+
+def _roofline(fam: str, stats: dict, prec: int, peaks: dict, peak_kind: str, ny: int = 0):
     """Roofline record for one kernel family from the library's profiler totals."""
     ms = stats["ms"]
     if ms <= 0:
         return None
+    if fam == "gemm" and prec != 0:
+        # 3xTF32 complex GEMMs on tcgen05: three tensor products per complex product, each
+        # the 4 real products of the complex multiply -> 3x the algorithmic complex flops
+        tflops = 3.0 * stats["flops"] / (ms * 1e-3) / 1e12
+        bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
+        peak = bf16 * TF32_OVER_BF16
+        return {"bound": "tensor", "achieved": round(tflops, 3), "peak": round(peak, 1),
+                "unit": "TFLOP/s", "frac": round(tflops / peak, 4), "traffic": None,
+                "kernel": fam, "peak_source": f"{peak_kind} sustained bf16 x 1.1/2.25 (TF32); "
+                "achieved counts the 3 TF32 products per complex product"}
     if fam in ("gemm", "invert", "level0"):
         tflops = stats["flops"] / (ms * 1e-3) / 1e12
         if prec == 0:
@@ -140,8 +159,13 @@ def _roofline(fam: str, stats: dict, prec: int, peaks: dict, peak_kind: str):
         else:
             peak = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
             src = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"
+        traffic = None
+        if fam == "invert" and prec != 0 and ny == 160:
+            blocks = stats["flops"] / (8.0 * ny ** 3)      # 8 ny^3 flops per block inverse
+            steps = max(1, stats.get("steps", 1))
+            traffic = round(GJ_FP32_DRAM_BYTES_PER_BLOCK_NY160 * blocks / steps)
         return {"bound": "alu", "achieved": round(tflops, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(tflops / peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(tflops / peak, 4), "traffic": traffic,
                 "kernel": fam, "peak_source": src}
     if fam == "qform":
         tflops = stats["flops"] / (ms * 1e-3) / 1e12
@@ -345,13 +369,14 @@ def run_ours(args):
     if rank == 0:
         fams = {f: v for f, v in prof.items() if v["ms"] > 0}
         dom = max(fams, key=lambda f: fams[f]["ms"])
-        roof = _roofline(dom, fams[dom], prec, peaks, peak_kind)
+        roof = _roofline(dom, dict(fams[dom], steps=K1), prec, peaks, peak_kind, ny=wl.grid.ny)
         kernels = {}
         for f, v in fams.items():
-            r = _roofline(f, v, prec, peaks, peak_kind)
+            r = _roofline(f, dict(v, steps=K1), prec, peaks, peak_kind, ny=wl.grid.ny)
             kernels[f] = {"ms_per_step": round(v["ms"] / K1, 4),
                           "share": round(v["ms"] / sum(x["ms"] for x in fams.values()), 4),
                           "launches_per_step": v["launches"] / K1,
+                          "bound": r["bound"] if r else None,
                           "achieved": r["achieved"] if r else None,
                           "unit": r["unit"] if r else None, "frac": r["frac"] if r else None}
         ps = sorted(per)
@@ -429,6 +454,38 @@ def run_ours(args):
                 "time_ratio_brute_over_reciprocal": round(tb / tr, 1),
                 "F_reciprocal": Fr, "F_bruteforce": Fb,
                 "rel_diff": abs(Fb - Fr) / abs(Fr)}
+        # cold evaluations with the adjoint width gradient on the gradient workload
+        # (C2's grid, virtual focus 20 wavelengths up, cone of +-15 degrees)
+        wg = W.c4_gradient()
+        with P.Grid(wg.grid, prec=prec, device=local, stream=stream) as g4:
+            t = []
+            for k in range(args.other_steps + 1):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g4.set_design(widths_dev[Wm + k % K])
+                g4.factor()
+                Fg, grad, ginfo = g4.avg_intensity_grad(wg.objective, wg.light)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if k:
+                    t.append(e0.elapsed_time(e1))
+            t.sort()
+            extra["gradient"] = {
+                "workload": wg.name, "evals_per_s": round(1e3 / (sum(t) / len(t)), 3),
+                "p50_ms": round(t[len(t) // 2], 3), "p99_ms": round(t[-1], 3), "steps": len(t),
+                "grad_norm_inf": float(np.max(np.abs(grad)))}
+            # 100 projected-gradient iterations from seed-0 widths, clamped to [0.08, 0.36]
+            from paper_2207_10701_gb300.design import optimize
+            import time
+            t0 = time.perf_counter()
+            res = optimize(g4, wg.objective, wg.light, W.widths(wg.grid.n_cells, 0), iters=100,
+                           step=0.01)
+            extra["design_loop"] = {
+                "workload": wg.name, "iterations": len(res.steps), "accepted": len(res.history) - 1,
+                "F_start": res.history[0], "F_end": res.history[-1],
+                "gain": round(res.history[-1] / res.history[0], 4),
+                "seconds": round(time.perf_counter() - t0, 2)}
         line.update(extra)
     if rank == 0 and not args.no_cpu_baseline and ws_ == 1:
         line["cpu_baseline"] = _cpu_baseline()
@@ -437,6 +494,89 @@ def run_ours(args):
     if ws_ > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    return 0
+
+
+def run_serve(args):
+    """Serving form: a stream of requests with Poisson arrivals (metasurfaces of 50..1250
+    cells, concentrator / collimator, cone / annulus, 30 % with the gradient) admitted
+    continuously by the library's server; p50/p99 latency from submission to result and
+    completed evaluations per second.  The arrival rate defaults to 70 % of the capacity
+    measured on a closed-loop burst of the same distribution."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    import paper_2207_10701_gb300 as P
+    from paper_2207_10701_gb300 import build as B
+
+    ws_, rank, local = _dist()
+    if rank != 0:
+        return 0
+    B.build()
+    torch.cuda.set_device(local)
+    slots, arena = args.serve_slots, int(args.serve_arena_gb * (1 << 30))
+    with P.Server(device=local, slots=slots, arena_bytes=arena, lookahead=8) as srv:
+        def run(reqs, paced):
+            t_start = time.perf_counter()
+            tickets = [None] * len(reqs)
+
+            def submitter():
+                for k, r in enumerate(reqs):
+                    if paced:
+                        dt = r.arrival_s - (time.perf_counter() - t_start)
+                        if dt > 0:
+                            time.sleep(dt)
+                    tickets[k] = srv.submit(r.grid, r.widths, r.objective, r.light,
+                                            want_grad=r.want_grad)
+            th = threading.Thread(target=submitter)
+            th.start()
+            out = []
+            for k in range(len(reqs)):
+                while tickets[k] is None:
+                    time.sleep(0.0005)
+                out.append(srv.wait(tickets[k], timeout=3600))
+            th.join()
+            return out
+
+        # warm-up (kernels loaded, arena touched) and closed-loop capacity
+        run(W.serving_requests(16, 0.0, seed=999), paced=False)
+        burst = run(W.serving_requests(args.serve_burst, 0.0, seed=998), paced=False)
+        span = (max(r["t_end_us"] for r in burst) - min(r["t_submit_us"] for r in burst)) * 1e-6
+        capacity = len(burst) / span
+        rate = args.serve_rate if args.serve_rate > 0 else 0.7 * capacity
+        reqs = W.serving_requests(args.serve_requests, rate, seed=1)
+        st0 = srv.stats()
+        clocks = ClockSampler(local)
+        clocks.start()
+        res = run(reqs, paced=True)
+        clk = clocks.stop()
+        st = srv.stats()
+    lat = np.array([(r["t_end_us"] - r["t_submit_us"]) * 1e-3 for r in res])
+    wait = np.array([(r["t_start_us"] - r["t_submit_us"]) * 1e-3 for r in res])
+    ok = [r["status"] in (0, 6) for r in res]
+    span = (max(r["t_end_us"] for r in res) - min(r["t_submit_us"] for r in res)) * 1e-6
+    grad = np.array([q.want_grad for q in reqs])
+    line = {
+        "metric": "serving: reciprocal evaluations/s under Poisson arrivals, p50/p99 latency",
+        "value": round(sum(ok) / span, 3), "unit": "evals/s", "n_gpus": 1,
+        "higher_is_better": True, "impl": "ours", "dtype": "f32+f64refine", "data": "synthetic",
+        "p50_ms": round(float(np.percentile(lat, 50)), 3),
+        "p99_ms": round(float(np.percentile(lat, 99)), 3),
+        "p50_queue_ms": round(float(np.percentile(wait, 50)), 3),
+        "p99_queue_ms": round(float(np.percentile(wait, 99)), 3),
+        "p50_ms_gradient": round(float(np.percentile(lat[grad], 50)), 3) if grad.any() else None,
+        "requests": len(reqs), "failed": len(reqs) - sum(ok),
+        "arrival_rate_per_s": round(rate, 3), "capacity_evals_per_s": round(capacity, 3),
+        "config": {"workload": "serving stream: 50-1250 cells log-uniform, ny 160, "
+                               "concentrator/collimator, cone/annulus, 30% gradient",
+                   "slots": slots, "arena_gb": args.serve_arena_gb, "lookahead": 8},
+        "server": {k: st[k] - st0.get(k, 0) if k in ("submitted", "completed", "failed",
+                                                     "admission_waits", "bypasses") else st[k]
+                   for k in st},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -452,7 +592,16 @@ def main():
                     help="independent evaluations in flight (one stream + host thread each)")
     ap.add_argument("--quick", action="store_true", help="skip the FP64 / brute-force extras")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving form instead of the evaluation benchmark")
+    ap.add_argument("--serve-requests", type=int, default=4096)
+    ap.add_argument("--serve-rate", type=float, default=0.0, help="arrivals/s (0: 70%% of capacity)")
+    ap.add_argument("--serve-slots", type=int, default=6)
+    ap.add_argument("--serve-burst", type=int, default=96)
+    ap.add_argument("--serve-arena-gb", type=float, default=96.0)
     args = ap.parse_args()
+    if args.serve:
+        return run_serve(args)
     if args.impl == "ours":
         args.warmup = max(3, args.warmup)   # never time fewer than 3 warm-up steps
     if args.impl == "reference":

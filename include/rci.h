@@ -115,7 +115,8 @@ typedef struct {
 
 typedef struct {
   int32_t refine_iters;  /* refinement steps taken by the last solve */
-  int32_t reserved;
+  int32_t fallback;      /* 1: an FP32_REFINE grid finished the solve on its FP64 fallback
+                            factorisation (see rci_set_refinement) */
   double rel_residual;   /* ||b - A x||_2 / ||b||_2 after the last solve (FP64 stencil) */
   double ms_factor;      /* device time of the last factorisation */
   double ms_solve;       /* device time of the last solve incl. refinement */
@@ -157,9 +158,14 @@ rci_status rci_solve(rci_grid* g, const double* b, double* x, int64_t nrhs, rci_
 
 /* Iterative refinement settings of the grid: stop when ||b - A x||_2 / ||b||_2 <= tol
  * (FP64 stencil residual) or after max_steps corrections (the first FP32 solve is not
- * counted).  Defaults: FP32_REFINE tol 1e-10, 12 steps; FP64 tol 1e-13, 2 steps.  A
- * solve that ends above tol returns RCI_ENOCONV with its best value (FP64 grids only
- * report ENOCONV above 1e-9).  tol > 0, 0 <= max_steps <= 100. */
+ * counted).  Defaults: FP32_REFINE tol 1e-10, 30 steps; FP64 tol 1e-13, 2 steps.
+ * An FP32_REFINE grid whose refinement fails -- a non-finite residual, a step that
+ * reduces the residual less than 0.7-fold (after the second), more than max_steps
+ * steps, or a zero FP32 pivot in rci_factor -- factors the current design once in FP64
+ * (the FP64 factor store is allocated the first time, from the grid's memory source)
+ * and finishes this and every later solve of that design on it (rci_info.fallback).
+ * A solve that ends above tol returns RCI_ENOCONV with its best value (FP64 and fallback
+ * solves only above 1e-9).  tol > 0, 0 <= max_steps <= 100. */
 rci_status rci_set_refinement(rci_grid* g, double tol, int32_t max_steps);
 
 /* Reciprocal solve of Eq. 7: v = A^{-dag} w = conj(A^{-1} conj(w)) (A symmetric).
@@ -249,6 +255,86 @@ rci_status rci_gauss_legendre(int64_t n, double a, double b, double* nodes, doub
  * eps: float64[nx*ny] ([i][j]);  y = A x: complex128[nx*ny] (FP64 stencil). */
 rci_status rci_get_eps(rci_grid* g, double* eps_out);
 rci_status rci_apply_operator(rci_grid* g, const double* x, double* y);
+
+/* Device bytes a grid of this descriptor holds once created: every buffer a single
+ * right-hand-side evaluation needs (operator, factor store, solve workspace), plus the
+ * gradient's buffers when with_gradient != 0, each allocation rounded up to 256 bytes.
+ * Computed on the host without touching the device.  bytes: HOST.
+ * Errors: EINVAL (bad descriptor). */
+rci_status rci_grid_footprint(const rci_grid_desc* desc, int with_gradient, size_t* bytes);
+
+/* ---- serving (continuous admission of many evaluations on one GPU) ----
+ * The paper's use of the method is many evaluations: inverse design (Sec. 5.1) over
+ * many designs and angular distributions.  A server runs `slots` workers (a host thread
+ * and a CUDA stream each) over one device-memory arena taken at creation, so requests of
+ * different sizes overlap on the device and admission never calls cudaMalloc/cudaFree.
+ * A request is admitted when a worker is free and its grid (rci_grid_footprint with the
+ * gradient buffers) can be carved out of the arena, after evicting resident
+ * factorisations that no request is using (least recently used first); otherwise it
+ * waits at the head of the queue for running requests to release memory.  A free worker
+ * may start one of the next `lookahead` queued requests that fits while the head does
+ * not (a head passed over 16 times is no longer overtaken).  A request that does not fit
+ * in the arena even when nothing else holds memory completes with RCI_ENOMEM.  Each
+ * evaluation is the one of rci_avg_intensity / rci_avg_intensity_grad on a grid of its
+ * own, so its result does not depend on what else is in flight. */
+typedef struct rci_server rci_server;
+
+typedef struct {
+  int32_t device;
+  int32_t slots;          /* concurrent evaluations, 1..64 */
+  uint64_t arena_bytes;   /* device memory taken at creation; 0: 90 % of the free memory */
+  uint64_t cache_bytes;   /* at most this much of the arena keeps keyed factorisations
+                             resident for reuse; 0: none are kept */
+  int32_t lookahead;      /* >= 0; 0: strict first-in first-out admission */
+  int32_t reserved;
+} rci_server_desc;
+
+typedef struct {
+  rci_grid_desc grid;     /* geometry and precision (grid.device is ignored: the server's) */
+  const double* widths;   /* HOST float64[grid.n_cells], copied by rci_server_submit */
+  rci_objective obj;      /* USER_ROW's w_row is copied by rci_server_submit */
+  rci_light light;        /* USER_LAGS's lags are copied by rci_server_submit */
+  int32_t want_grad;      /* != 0: also dF/dwidths (rci_avg_intensity_grad) */
+  int32_t reserved;
+  uint64_t design_key;    /* != 0: the factorised grid may stay resident, and a later request
+                             with the same key, descriptor and widths reuses it */
+  double* grad_out;       /* HOST float64[grid.n_cells] when want_grad; owned by the caller,
+                             must stay valid until the request completes; written before it
+                             completes */
+} rci_request;
+
+typedef struct {
+  int32_t status;         /* rci_status of the evaluation (RCI_ENOMEM: never fits) */
+  int32_t cache_hit;      /* 1: a resident factorisation was reused */
+  double value;           /* the averaged intensity F */
+  int32_t refine_iters;
+  int32_t reserved;
+  double rel_residual;
+  double t_submit_us;     /* server clock: microseconds since rci_server_create */
+  double t_start_us;      /* admitted (grid ready) */
+  double t_end_us;        /* result ready */
+  uint64_t footprint;     /* device bytes of the request's grid */
+} rci_result;
+
+typedef struct {
+  uint64_t submitted, completed, failed, cache_hits, cache_evictions, admission_waits, bypasses;
+  int32_t in_flight, queued, resident, reserved;
+  uint64_t arena_bytes, arena_used, arena_peak, cache_bytes;
+} rci_server_stats;
+
+/* Start a server (allocates the arena, creates the streams and workers).
+ * Errors: EINVAL (bad descriptor), ENOMEM (arena), ECUDA. */
+rci_status rci_server_create(const rci_server_desc* desc, rci_server** out);
+/* Queue a request; returns at once with a ticket (HOST).  Inputs are copied.
+ * Errors: EINVAL (bad request), ESTATE (server stopping). */
+rci_status rci_server_submit(rci_server* s, const rci_request* req, uint64_t* ticket);
+/* Wait for a ticket's result (HOST), timeout_s < 0: no limit.  Each ticket's result is
+ * delivered once.  Errors: EINVAL (unknown or collected ticket), ETIMEOUT. */
+rci_status rci_server_wait(rci_server* s, uint64_t ticket, double timeout_s, rci_result* out);
+/* Counters and memory use.  out: HOST. */
+rci_status rci_server_stats_read(rci_server* s, rci_server_stats* out);
+/* Finish every queued request, stop the workers, release all device memory. */
+rci_status rci_server_destroy(rci_server* s);
 
 /* ---- instrumentation (no counterpart in the paper; measurement support) ----
  * Kernel families timed by the profiler:

@@ -1376,10 +1376,11 @@ struct BcrHandle {
   int ws_nrhs = 0;
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  DevMem mem;
 };
 
 static void free_ws(BcrHandle* h) {
-  if (h->ws) cudaFree(h->ws);
+  h->mem.release(h->ws);
   h->ws = nullptr;
   h->ws_nrhs = 0;
   h->ws_bytes = 0;
@@ -1389,8 +1390,7 @@ void bcr_destroy(BcrHandle* h) {
   if (!h) return;
   void* ps[] = {h->tdl, h->tdinv, h->tdu, h->tdu2, h->tpiv, h->G0, h->Dw[0], h->Dw[1],
                 h->Lw[0], h->Lw[1], h->store, h->status};
-  for (void* p : ps)
-    if (p) cudaFree(p);
+  for (void* p : ps) h->mem.release(p);
   free_ws(h);
   delete h;
 }
@@ -1399,11 +1399,12 @@ size_t bcr_bytes(const BcrHandle* h) { return h->factor_bytes + h->ws_bytes; }
 void bcr_set_profiler(BcrHandle* h, Profiler* p) { h->prof = p; }
 int bcr_precision(const BcrHandle* h) { return h->prec; }
 
-cudaError_t bcr_create(int nx, int ny, int prec, BcrHandle** out, size_t* bytes) {
+cudaError_t bcr_create(int nx, int ny, int prec, const DevMem* mem, BcrHandle** out, size_t* bytes) {
   *out = nullptr;
   if (nx < 1 || ny < 2 || ny > 1024) return cudaErrorInvalidValue;
   BcrHandle* h = new (std::nothrow) BcrHandle();
   if (!h) return cudaErrorMemoryAllocation;
+  if (mem) h->mem = *mem;
   h->prec = prec;
   h->nx = nx;
   h->ny = ny;
@@ -1433,7 +1434,7 @@ cudaError_t bcr_create(int nx, int ny, int prec, BcrHandle** out, size_t* bytes)
   cudaError_t e = cudaSuccess;
   auto alloc = [&](void** p, size_t b) {
     if (e != cudaSuccess) return;
-    e = cudaMalloc(p, b < 16 ? 16 : b);
+    e = h->mem.alloc(p, b);
     if (e == cudaSuccess) h->factor_bytes += b;
   };
   size_t m0b = (size_t)std::max<int64_t>(m0, 1) * ny;
@@ -1561,6 +1562,16 @@ static int64_t ws_elems(const BcrHandle* h, int nrhs) {
   return tot;
 }
 
+cudaError_t bcr_reserve_ws(BcrHandle* h, int nrhs) {
+  if (h->ws_nrhs >= nrhs) return cudaSuccess;
+  free_ws(h);
+  size_t bytes = (size_t)ws_elems(h, nrhs) * h->esz;
+  RCI_CUDA_TRY(h->mem.alloc(&h->ws, bytes));
+  h->ws_bytes = bytes;
+  h->ws_nrhs = nrhs;
+  return cudaSuccess;
+}
+
 template <typename T>
 static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cplx<T>* x, int nrhs,
                            cudaStream_t s) {
@@ -1568,13 +1579,7 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
   const int64_t nn = (int64_t)ny * ny;
   const int64_t row = (int64_t)ny * nrhs;
   const int m0 = (int)h->m[0], n1 = (nx + 1) / 2;
-  if (h->ws_nrhs < nrhs) {
-    free_ws(h);
-    size_t bytes = (size_t)ws_elems(h, nrhs) * sizeof(cplx<T>);
-    RCI_CUDA_TRY(cudaMalloc(&h->ws, bytes));
-    h->ws_bytes = bytes;
-    h->ws_nrhs = nrhs;
-  }
+  RCI_CUDA_TRY(bcr_reserve_ws(h, nrhs));
   // carve the workspace
   cplx<T>* p = (cplx<T>*)h->ws;
   cplx<T>* t0 = p;

@@ -21,8 +21,12 @@
 
 struct BcrHandle;
 
-// prec: RCI_FP64 -> double, RCI_FP32_REFINE -> float.  Allocates the factor store.
-cudaError_t bcr_create(int nx, int ny, int prec, BcrHandle** out, size_t* bytes);
+// prec: RCI_FP64 -> double, RCI_FP32_REFINE -> float.  Allocates the factor store from
+// mem (cudaMalloc when mem is null).  No kernel is launched.
+cudaError_t bcr_create(int nx, int ny, int prec, const DevMem* mem, BcrHandle** out, size_t* bytes);
+// Allocate the solve workspace for nrhs right-hand sides now (otherwise the first solve
+// with more right-hand sides than before allocates it).
+cudaError_t bcr_reserve_ws(BcrHandle* h, int nrhs);
 void bcr_destroy(BcrHandle* h);
 size_t bcr_bytes(const BcrHandle* h);
 

@@ -49,6 +49,12 @@ struct rci_grid {
   void *m32a = nullptr, *m32b = nullptr;
   double *th_d = nullptr, *wq_d = nullptr, *f_d = nullptr;
   int th_cap = 0;
+  // FP64 fallback of an FP32 grid: an FP64 factorisation made when refinement on the FP32
+  // one fails (non-finite, stagnating or out of steps), used until the next design
+  BcrHandle* bcr64 = nullptr;
+  bool use64 = false;
+  double2* corr64 = nullptr;
+  int64_t corr64_n = 0;
   // gradient buffers (allocated by the first gradient call)
   double2 *mu = nullptr, *gsrc = nullptr, *tpart = nullptr;
   double* dgrad = nullptr;
@@ -57,11 +63,12 @@ struct rci_grid {
   rci_light lags_key{};
   // settings
   double tol32 = 1e-10, tol64 = 1e-13;
-  int max_refine32 = 12, max_refine64 = 2;
+  int max_refine32 = 31, max_refine64 = 2;  // FP32: solves, the first one included
   size_t bytes = 0;
   cudaEvent_t ev[6] = {};
   Profiler prof;
   std::string err;
+  DevMem mem;  // device memory source (cudaMalloc unless a serving arena supplies one)
 };
 
 namespace {
@@ -87,14 +94,12 @@ rci_status cuda_fail(rci_grid* g, cudaError_t e, const char* where) {
 
 template <typename P>
 cudaError_t dalloc(rci_grid* g, P** p, size_t bytes) {
-  cudaError_t e = cudaMalloc((void**)p, bytes < 16 ? 16 : bytes);
+  cudaError_t e = g->mem.alloc((void**)p, bytes);
   if (e == cudaSuccess) g->bytes += bytes;
   return e;
 }
 
-void dfree(void* p) {
-  if (p) cudaFree(p);
-}
+void dfree(rci_grid* g, void* p) { g->mem.release(p); }
 
 bool desc_ok(const rci_grid_desc* d, std::string& why) {
   if (d->n_cells < 1 || d->cell_px < 1 || d->ppl < 2 || d->npml < 1 || d->ny < 4) {
@@ -240,11 +245,11 @@ rci_status build_objective(rci_grid* g, const rci_objective* o, double2* b) {
 
 rci_status ensure_multi(rci_grid* g, int nq) {
   if (g->mq_cap >= nq) return RCI_OK;
-  dfree(g->mb);
-  dfree(g->mx);
-  dfree(g->mr);
-  dfree(g->m32a);
-  dfree(g->m32b);
+  dfree(g, g->mb);
+  dfree(g, g->mx);
+  dfree(g, g->mr);
+  dfree(g, g->m32a);
+  dfree(g, g->m32b);
   g->mb = g->mx = g->mr = nullptr;
   g->m32a = g->m32b = nullptr;
   size_t n = (size_t)g->N * nq;
@@ -288,53 +293,115 @@ rci_status residual_ratio(rci_grid* g, const double2* b, const double2* x, doubl
   return RCI_OK;
 }
 
+// FP64 refinement on an FP64 factorisation h: x = A^-1 b, then corrections d while the
+// FP64 stencil residual is above tol64 (at most max_refine64 steps).
+rci_status solve64(rci_grid* g, BcrHandle* h, const double2* b, double2* x, double2* r, double2* d,
+                   int nrhs, int* it, double* worst) {
+  const int64_t n = g->N * nrhs;
+  CK(bcr_solve(h, g->cx, b, x, nrhs, g->s), "solve");
+  rci_status st = residual_ratio(g, b, x, r, nrhs, worst);
+  if (st != RCI_OK) return st;
+  while (*worst > g->tol64 && *it < g->max_refine64) {
+    CK(bcr_solve(h, g->cx, r, d, nrhs, g->s), "refine solve");
+    CK(launch_axpy64(x, d, n, g->s), "refine update");
+    ++*it;
+    st = residual_ratio(g, b, x, r, nrhs, worst);
+    if (st != RCI_OK) return st;
+  }
+  return RCI_OK;
+}
+
+// Factor the current design in FP64 for an FP32 grid whose refinement failed (the
+// classic fallback of mixed-precision solvers, e.g. LAPACK's single/double refinement
+// driver): the FP64 factor store is allocated the first time and kept for later designs.
+rci_status fp64_fallback(rci_grid* g) {
+  if (g->use64) return RCI_OK;
+  if (!g->bcr64) {
+    CK(bcr_create(g->g.nx, g->g.ny, RCI_FP64, &g->mem, &g->bcr64, nullptr), "FP64 fallback store");
+    bcr_set_profiler(g->bcr64, &g->prof);
+  }
+  CK(bcr_factor(g->bcr64, g->dg, g->cx, g->cy, g->s), "FP64 fallback factor");
+  int32_t st = 0;
+  CK(bcr_read_status(g->bcr64, &st, g->s), "FP64 fallback status");
+  if (st == DEV_SINGULAR) return fail(g, RCI_ESINGULAR, "zero pivot in a diagonal block (FP64)");
+  g->use64 = true;
+  return RCI_OK;
+}
+
+rci_status ensure_corr64(rci_grid* g, int64_t n) {
+  if (g->corr64_n >= n) return RCI_OK;
+  dfree(g, g->corr64);
+  g->corr64 = nullptr;
+  g->corr64_n = 0;
+  CK(dalloc(g, &g->corr64, sizeof(double2) * n), "FP64 fallback correction");
+  g->corr64_n = n;
+  return RCI_OK;
+}
+
 // Solve A x = b (FP64 in/out, device, nrhs columns) with the grid's factorisation and
 // iterative refinement on the FP64 stencil residual.  r, a32, b32 are scratch buffers of
 // the same length: complex64 for FP32 grids; for FP64 grids a32 is complex128 (the
-// correction) and b32 is unused.
+// correction) and b32 is unused.  An FP32 grid refines while each step reduces the
+// residual at least 0.7-fold, up to max_refine32 steps; a non-finite residual, stagnation
+// or running out of steps switches it to its FP64 fallback factorisation.
 rci_status refined_solve(rci_grid* g, const double2* b, double2* x, double2* r, void* a32,
                          void* b32, int nrhs, rci_info* info) {
   const int64_t n = g->N * nrhs;
   double worst = 0.0;
   int it = 0;
+  bool fell_back = false;
   rci_status st = RCI_OK;
   if (g->d.prec == RCI_FP64) {
-    double2* d = (double2*)a32;
-    CK(bcr_solve(g->bcr, g->cx, b, x, nrhs, g->s), "solve");
-    st = residual_ratio(g, b, x, r, nrhs, &worst);
+    st = solve64(g, g->bcr, b, x, r, (double2*)a32, nrhs, &it, &worst);
     if (st != RCI_OK) return st;
-    while (worst > g->tol64 && it < g->max_refine64) {
-      CK(bcr_solve(g->bcr, g->cx, r, d, nrhs, g->s), "refine solve");
-      CK(launch_axpy64(x, d, n, g->s), "refine update");
-      ++it;
-      st = residual_ratio(g, b, x, r, nrhs, &worst);
-      if (st != RCI_OK) return st;
-    }
   } else {
-    CK(cudaMemsetAsync(x, 0, sizeof(double2) * n, g->s), "zero x");
-    CK(cudaMemcpyAsync(r, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, g->s), "copy b");
-    worst = 1.0;
-    while (true) {
-      CK(launch_to_f32(r, (float2*)a32, n, g->s), "to fp32");
-      CK(bcr_solve(g->bcr, g->cx, a32, b32, nrhs, g->s), "fp32 solve");
-      CK(launch_add_f32(x, (const float2*)b32, n, g->s), "update");
-      ++it;
-      st = residual_ratio(g, b, x, r, nrhs, &worst);
-      if (st != RCI_OK) return st;
-      if (worst <= g->tol32 || it >= g->max_refine32) break;
+    bool need64 = g->use64;
+    if (!need64) {
+      CK(cudaMemsetAsync(x, 0, sizeof(double2) * n, g->s), "zero x");
+      CK(cudaMemcpyAsync(r, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, g->s), "copy b");
+      double prev = 1.0;
+      while (true) {
+        CK(launch_to_f32(r, (float2*)a32, n, g->s), "to fp32");
+        CK(bcr_solve(g->bcr, g->cx, a32, b32, nrhs, g->s), "fp32 solve");
+        CK(launch_add_f32(x, (const float2*)b32, n, g->s), "update");
+        ++it;
+        st = residual_ratio(g, b, x, r, nrhs, &worst);
+        if (st == RCI_ENUMERIC) {
+          need64 = true;
+          break;
+        }
+        if (st != RCI_OK) return st;
+        if (worst <= g->tol32) break;
+        if (it >= g->max_refine32 || (it >= 3 && worst > 0.7 * prev)) {
+          need64 = true;
+          break;
+        }
+        prev = worst;
+      }
+      it -= 1;  // the first FP32 solve is not a refinement step
     }
-    it -= 1;  // the first FP32 solve is not a refinement step
+    if (need64) {
+      st = fp64_fallback(g);
+      if (st != RCI_OK) return st;
+      st = ensure_corr64(g, n);
+      if (st != RCI_OK) return st;
+      it = 0;
+      st = solve64(g, g->bcr64, b, x, r, g->corr64, nrhs, &it, &worst);
+      if (st != RCI_OK) return st;
+      fell_back = true;
+    }
   }
   if (info) {
     info->refine_iters = it;
     info->rel_residual = worst;
+    info->fallback = fell_back ? 1 : 0;
   }
   if (nrhs > 1) {  // the multi-RHS solve runs tensor-core GEMMs with bounded waits
     int32_t dst = 0;
     CK(bcr_read_status(g->bcr, &dst, g->s), "solve status");
     if (dst == DEV_TIMEOUT) return fail(g, RCI_ETIMEOUT, "a bounded tensor-core wait expired");
   }
-  double tol = g->d.prec == RCI_FP64 ? 1e-9 : g->tol32;
+  double tol = (g->d.prec == RCI_FP64 || fell_back) ? 1e-9 : g->tol32;
   if (worst > tol) return fail(g, RCI_ENOCONV, "iterative refinement did not converge");
   return RCI_OK;
 }
@@ -395,9 +462,9 @@ rci_status run_angles(rci_grid* g, const rci_objective* o, const double* th_dev,
 
 rci_status ensure_theta(rci_grid* g, int nq) {
   if (g->th_cap >= nq) return RCI_OK;
-  dfree(g->th_d);
-  dfree(g->wq_d);
-  dfree(g->f_d);
+  dfree(g, g->th_d);
+  dfree(g, g->wq_d);
+  dfree(g, g->f_d);
   g->th_d = g->wq_d = g->f_d = nullptr;
   CK(dalloc(g, &g->th_d, sizeof(double) * nq), "angles");
   CK(dalloc(g, &g->wq_d, sizeof(double) * nq), "angles");
@@ -447,9 +514,10 @@ rci_status rci_destroy_grid(rci_grid* g) {
   void* ps[] = {g->widths, g->eps, g->dg, g->cx, g->cy, g->dg0, g->kss, g->b1, g->x1, g->r1, g->r32, g->d32,
                 g->crow, g->vsrc, g->lags, g->qpart, g->dscal, g->part_r, g->part_b, g->ratio,
                 g->vf_scratch, g->dstatus, g->mb, g->mx, g->mr, g->m32a, g->m32b, g->th_d,
-                g->wq_d, g->f_d, g->mu, g->gsrc, g->tpart, g->dgrad};
-  for (void* p : ps) dfree(p);
+                g->wq_d, g->f_d, g->mu, g->gsrc, g->tpart, g->dgrad, g->corr64};
+  for (void* p : ps) dfree(g, p);
   bcr_destroy(g->bcr);
+  bcr_destroy(g->bcr64);
   if (g->prof.pool) {
     for (int i = 0; i < g->prof.cap; ++i) cudaEventDestroy(g->prof.pool[i]);
     delete[] g->prof.pool;
@@ -461,70 +529,166 @@ rci_status rci_destroy_grid(rci_grid* g) {
   return RCI_OK;
 }
 
-rci_status rci_create_grid(const rci_grid_desc* desc, void* stream, rci_grid** out) {
+}  // extern "C"
+
+namespace {
+
+// Gradient buffers: the adjoint field, W v on the source plane and its partials, dF/dw.
+cudaError_t alloc_grad_buffers(rci_grid* g) {
+  if (g->mu) return cudaSuccess;
+  const int64_t ns = g->g.n_src;
+  RCI_CUDA_TRY(dalloc(g, &g->mu, sizeof(double2) * g->N));
+  RCI_CUDA_TRY(dalloc(g, &g->gsrc, sizeof(double2) * ns));
+  RCI_CUDA_TRY(dalloc(g, &g->tpart, sizeof(double2) * ns * toeplitz_mv_chunks(ns)));
+  RCI_CUDA_TRY(dalloc(g, &g->dgrad, sizeof(double) * g->d.n_cells));
+  return cudaSuccess;
+}
+
+// Every device buffer a single-RHS evaluation needs (and the gradient's when asked), from
+// g->mem.  No kernel launch, no event, no synchronisation: with a counting allocator this
+// is the exact footprint of the grid.
+cudaError_t grid_alloc(rci_grid* g, bool with_grad) {
+  const int64_t N = g->N, ns = g->g.n_src;
+  const rci_grid_desc* desc = &g->d;
+  RCI_CUDA_TRY(dalloc(g, &g->widths, sizeof(double) * desc->n_cells));
+  RCI_CUDA_TRY(dalloc(g, &g->eps, sizeof(double) * N));
+  RCI_CUDA_TRY(dalloc(g, &g->dg, sizeof(double2) * N));
+  RCI_CUDA_TRY(dalloc(g, &g->cx, sizeof(double2) * N));
+  RCI_CUDA_TRY(dalloc(g, &g->cy, sizeof(double2) * N));
+  RCI_CUDA_TRY(dalloc(g, &g->dg0, sizeof(double2) * N));
+  RCI_CUDA_TRY(dalloc(g, &g->kss, sizeof(double2) * N));
+  RCI_CUDA_TRY(dalloc(g, &g->b1, sizeof(double2) * N));
+  RCI_CUDA_TRY(dalloc(g, &g->x1, sizeof(double2) * N));
+  RCI_CUDA_TRY(dalloc(g, &g->r1, sizeof(double2) * N));
+  if (desc->prec == RCI_FP32_REFINE) {
+    RCI_CUDA_TRY(dalloc(g, &g->r32, sizeof(float2) * N));
+    RCI_CUDA_TRY(dalloc(g, &g->d32, sizeof(float2) * N));
+  } else {
+    RCI_CUDA_TRY(dalloc(g, &g->r32, sizeof(double2) * N));  // FP64 refinement corrections
+  }
+  RCI_CUDA_TRY(dalloc(g, &g->crow, sizeof(double2) * ns));
+  RCI_CUDA_TRY(dalloc(g, &g->vsrc, sizeof(double2) * ns));
+  RCI_CUDA_TRY(dalloc(g, &g->lags, sizeof(double) * ns));
+  RCI_CUDA_TRY(dalloc(g, &g->qpart, sizeof(double) * qform_num_partials(ns)));
+  RCI_CUDA_TRY(dalloc(g, &g->dscal, sizeof(double) * 8));
+  RCI_CUDA_TRY(dalloc(g, &g->part_r, sizeof(double) * residual_blocks(g->g) * MAXQ));
+  RCI_CUDA_TRY(dalloc(g, &g->part_b, sizeof(double) * residual_blocks(g->g) * MAXQ));
+  RCI_CUDA_TRY(dalloc(g, &g->ratio, sizeof(double) * MAXQ));
+  RCI_CUDA_TRY(dalloc(g, &g->vf_scratch, sizeof(double) * (2 * VF_ORDER + 6 * VF_NODES)));
+  RCI_CUDA_TRY(dalloc(g, &g->dstatus, sizeof(int32_t)));
+  RCI_CUDA_TRY(bcr_create(g->g.nx, g->g.ny, desc->prec, &g->mem, &g->bcr, nullptr));
+  RCI_CUDA_TRY(bcr_reserve_ws(g->bcr, 1));
+  if (with_grad) RCI_CUDA_TRY(alloc_grad_buffers(g));
+  return cudaSuccess;
+}
+
+rci_grid* grid_shell(const rci_grid_desc* desc, cudaStream_t s, const DevMem* mem) {
+  rci_grid* g = new (std::nothrow) rci_grid();
+  if (!g) return nullptr;
+  g->d = *desc;
+  g->g = make_geom(*desc);
+  g->s = s;
+  g->device = desc->device;
+  g->N = (int64_t)g->g.nx * g->g.ny;
+  if (mem) g->mem = *mem;
+  return g;
+}
+
+struct CountingArena {
+  size_t total = 0;
+  uintptr_t next = 4096;
+};
+cudaError_t counting_alloc(void* ctx, void** p, size_t bytes) {
+  auto* c = static_cast<CountingArena*>(ctx);
+  const size_t b = (bytes + 255) & ~(size_t)255;
+  c->total += b;
+  *p = reinterpret_cast<void*>(c->next);
+  c->next += b;
+  return cudaSuccess;
+}
+void counting_free(void*, void*) {}
+
+}  // namespace
+
+// Allocate a grid whose device memory comes from mem (nullptr: cudaMalloc), with the
+// gradient buffers up front when asked.  Host bookkeeping and allocations only: no kernel,
+// no event, no synchronisation (the serving runtime calls this under its admission lock).
+rci_status rci_grid_alloc_with(const rci_grid_desc* desc, cudaStream_t stream, const DevMem* mem,
+                               int with_grad, rci_grid** out) {
   if (!desc || !out) return RCI_EINVAL;
   *out = nullptr;
   std::string why;
   if (!desc_ok(desc, why)) return RCI_EINVAL;
-  rci_grid* g = new (std::nothrow) rci_grid();
-  if (!g) return RCI_ENOMEM;
-  g->d = *desc;
-  g->g = make_geom(*desc);
-  g->s = (cudaStream_t)stream;
-  g->device = desc->device;
-  g->N = (int64_t)g->g.nx * g->g.ny;
   int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || desc->device < 0 || desc->device >= ndev) {
-    delete g;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || desc->device < 0 || desc->device >= ndev)
     return RCI_ECUDA;
-  }
+  rci_grid* g = grid_shell(desc, stream, mem);
+  if (!g) return RCI_ENOMEM;
   DeviceGuard guard(g->device);
-  auto bail = [&](rci_status st) {
+  cudaError_t e = grid_alloc(g, with_grad != 0);
+  if (e != cudaSuccess) {
     rci_destroy_grid(g);
-    return st;
-  };
-#define CKC(expr)                                                             \
-  do {                                                                        \
-    cudaError_t _e = (expr);                                                  \
-    if (_e != cudaSuccess)                                                    \
-      return bail(_e == cudaErrorMemoryAllocation ? RCI_ENOMEM : RCI_ECUDA);  \
-  } while (0)
-  const int64_t N = g->N, ns = g->g.n_src;
-  CKC(dalloc(g, &g->widths, sizeof(double) * desc->n_cells));
-  CKC(dalloc(g, &g->eps, sizeof(double) * N));
-  CKC(dalloc(g, &g->dg, sizeof(double2) * N));
-  CKC(dalloc(g, &g->cx, sizeof(double2) * N));
-  CKC(dalloc(g, &g->cy, sizeof(double2) * N));
-  CKC(dalloc(g, &g->dg0, sizeof(double2) * N));
-  CKC(dalloc(g, &g->kss, sizeof(double2) * N));
-  CKC(dalloc(g, &g->b1, sizeof(double2) * N));
-  CKC(dalloc(g, &g->x1, sizeof(double2) * N));
-  CKC(dalloc(g, &g->r1, sizeof(double2) * N));
-  if (desc->prec == RCI_FP32_REFINE) {
-    CKC(dalloc(g, &g->r32, sizeof(float2) * N));
-    CKC(dalloc(g, &g->d32, sizeof(float2) * N));
-  } else {
-    CKC(dalloc(g, &g->r32, sizeof(double2) * N));  // FP64 refinement corrections
+    return e == cudaErrorMemoryAllocation ? RCI_ENOMEM : RCI_ECUDA;
   }
-  CKC(dalloc(g, &g->crow, sizeof(double2) * ns));
-  CKC(dalloc(g, &g->vsrc, sizeof(double2) * ns));
-  CKC(dalloc(g, &g->lags, sizeof(double) * ns));
-  CKC(dalloc(g, &g->qpart, sizeof(double) * qform_num_partials(ns)));
-  CKC(dalloc(g, &g->dscal, sizeof(double) * 8));
-  CKC(dalloc(g, &g->part_r, sizeof(double) * residual_blocks(g->g) * MAXQ));
-  CKC(dalloc(g, &g->part_b, sizeof(double) * residual_blocks(g->g) * MAXQ));
-  CKC(dalloc(g, &g->ratio, sizeof(double) * MAXQ));
-  CKC(dalloc(g, &g->vf_scratch, sizeof(double) * (2 * VF_ORDER + 6 * VF_NODES)));
-  CKC(dalloc(g, &g->dstatus, sizeof(int32_t)));
-  CKC(cudaMemsetAsync(g->cx, 0, sizeof(double2) * N, g->s));
-  CKC(launch_pml_coefficients(g->g, g->dg0, g->kss, g->cx, g->cy, g->s));
-  for (auto& e : g->ev) CKC(cudaEventCreate(&e));
-  size_t fb = 0;
-  CKC(bcr_create(g->g.nx, g->g.ny, desc->prec, &g->bcr, &fb));
-  g->bytes += fb;
-  CKC(cudaStreamSynchronize(g->s));
-#undef CKC
   *out = g;
+  return RCI_OK;
+}
+
+// Second half of grid creation: the design-independent stencil coefficients and the
+// events, then a synchronisation of the grid's stream.  On failure the caller destroys g.
+rci_status rci_grid_init(rci_grid* g) {
+  DeviceGuard guard(g->device);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(g->cx, 0, sizeof(double2) * g->N, g->s)) != cudaSuccess ||
+      (e = launch_pml_coefficients(g->g, g->dg0, g->kss, g->cx, g->cy, g->s)) != cudaSuccess)
+    return cuda_fail(g, e, "grid setup");
+  for (auto& ev : g->ev)
+    if (!ev && (e = cudaEventCreateWithFlags(&ev, cudaEventDefault)) != cudaSuccess)
+      return cuda_fail(g, e, "events");
+  if ((e = cudaStreamSynchronize(g->s)) != cudaSuccess) return cuda_fail(g, e, "grid setup");
+  return RCI_OK;
+}
+
+rci_status rci_grid_create_with(const rci_grid_desc* desc, cudaStream_t stream, const DevMem* mem,
+                                int with_grad, rci_grid** out) {
+  rci_status st = rci_grid_alloc_with(desc, stream, mem, with_grad, out);
+  if (st != RCI_OK) return st;
+  st = rci_grid_init(*out);
+  if (st != RCI_OK) {
+    rci_destroy_grid(*out);
+    *out = nullptr;
+  }
+  return st;
+}
+
+// Point the grid's work at another stream (the grid must be idle: every call of the ABI
+// returns with its stream drained or its results still to be read on that stream).
+void rci_grid_rebind_stream(rci_grid* g, cudaStream_t s) {
+  if (g) g->s = s;
+}
+
+extern "C" {
+
+rci_status rci_create_grid(const rci_grid_desc* desc, void* stream, rci_grid** out) {
+  return rci_grid_create_with(desc, (cudaStream_t)stream, nullptr, 0, out);
+}
+
+rci_status rci_grid_footprint(const rci_grid_desc* desc, int with_gradient, size_t* bytes) {
+  if (!desc || !bytes) return RCI_EINVAL;
+  std::string why;
+  if (!desc_ok(desc, why)) return RCI_EINVAL;
+  CountingArena c;
+  DevMem m;
+  m.ctx = &c;
+  m.alloc_fn = counting_alloc;
+  m.free_fn = counting_free;
+  rci_grid* g = grid_shell(desc, nullptr, &m);
+  if (!g) return RCI_ENOMEM;
+  cudaError_t e = grid_alloc(g, with_gradient != 0);
+  bcr_destroy(g->bcr);
+  delete g;
+  if (e != cudaSuccess) return RCI_EINVAL;
+  *bytes = c.total;
   return RCI_OK;
 }
 
@@ -562,6 +726,7 @@ rci_status rci_set_design(rci_grid* g, const double* widths, int64_t n_cells, in
   }
   g->has_design = true;
   g->factored = false;
+  g->use64 = false;
   return RCI_OK;
 }
 
@@ -581,7 +746,11 @@ rci_status rci_factor(rci_grid* g) {
     return fail(g, RCI_EINVAL, "a device width lies outside (0, period)");
   }
   if (st == DEV_TIMEOUT) return fail(g, RCI_ETIMEOUT, "a bounded tensor-core wait expired");
-  if (st == DEV_SINGULAR) return fail(g, RCI_ESINGULAR, "zero pivot in a diagonal block");
+  if (st == DEV_SINGULAR) {
+    if (g->d.prec == RCI_FP64) return fail(g, RCI_ESINGULAR, "zero pivot in a diagonal block");
+    rci_status fs = fp64_fallback(g);  // an FP32 pivot vanished: factor this design in FP64
+    if (fs != RCI_OK) return fs;
+  }
   g->factored = true;
   return RCI_OK;
 }
@@ -671,12 +840,7 @@ rci_status rci_avg_intensity_grad(rci_grid* g, const rci_objective* obj, const r
   if (st != RCI_OK) return st;
   const GridGeom& G = g->g;
   const int64_t ns = G.n_src;
-  if (!g->mu) {
-    CK(dalloc(g, &g->mu, sizeof(double2) * g->N), "gradient buffers");
-    CK(dalloc(g, &g->gsrc, sizeof(double2) * ns), "gradient buffers");
-    CK(dalloc(g, &g->tpart, sizeof(double2) * ns * toeplitz_mv_chunks(ns)), "gradient buffers");
-    CK(dalloc(g, &g->dgrad, sizeof(double) * g->d.n_cells), "gradient buffers");
-  }
+  CK(alloc_grad_buffers(g), "gradient buffers");
   // forward: z = A^{-1} conj(w) in x1, v on the source plane, F = v^dag W v
   rci_info i1{};
   rci_status s1 = reciprocal_solve(g, obj, &i1);
@@ -724,6 +888,7 @@ rci_status rci_avg_intensity_grad(rci_grid* g, const rci_objective* obj, const r
   if (info) {
     info->refine_iters = i1.refine_iters > i2.refine_iters ? i1.refine_iters : i2.refine_iters;
     info->rel_residual = i1.rel_residual > i2.rel_residual ? i1.rel_residual : i2.rel_residual;
+    info->fallback = i1.fallback | i2.fallback;
     float ms = 0;
     cudaEventElapsedTime(&ms, g->ev[2], g->ev[3]);
     info->ms_solve = i1.ms_solve + ms;

@@ -71,6 +71,27 @@ enum : int32_t { DEV_OK = 0, DEV_SINGULAR = 1, DEV_NONFINITE = 2, DEV_BADINPUT =
 
 static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// ---------------------------------------------------------------- device memory source
+// Where a grid and its factorisation get their device memory: cudaMalloc / cudaFree by
+// default, or an allocator supplied by the caller (the serving runtime's arena, whose
+// allocations and releases never synchronise the device).
+struct DevMem {
+  void* ctx = nullptr;
+  cudaError_t (*alloc_fn)(void* ctx, void** p, size_t bytes) = nullptr;
+  void (*free_fn)(void* ctx, void* p) = nullptr;
+  cudaError_t alloc(void** p, size_t bytes) const {
+    if (bytes < 16) bytes = 16;
+    return alloc_fn ? alloc_fn(ctx, p, bytes) : cudaMalloc(p, bytes);
+  }
+  void release(void* p) const {
+    if (!p) return;
+    if (free_fn)
+      free_fn(ctx, p);
+    else
+      cudaFree(p);
+  }
+};
+
 // ---------------------------------------------------------------- instrumentation
 // Process-wide count of kernel launches made by this library (every launch site calls
 // rci_note_launch), and an optional per-grid profiler that brackets kernel families

@@ -40,9 +40,36 @@ class LightC(C.Structure):
 
 
 class InfoC(C.Structure):
-    _fields_ = [("refine_iters", C.c_int32), ("reserved", C.c_int32),
+    _fields_ = [("refine_iters", C.c_int32), ("fallback", C.c_int32),
                 ("rel_residual", C.c_double), ("ms_factor", C.c_double),
                 ("ms_solve", C.c_double), ("ms_qform", C.c_double)]
+
+
+class ServerDescC(C.Structure):
+    _fields_ = [("device", C.c_int32), ("slots", C.c_int32), ("arena_bytes", C.c_uint64),
+                ("cache_bytes", C.c_uint64), ("lookahead", C.c_int32), ("reserved", C.c_int32)]
+
+
+class RequestC(C.Structure):
+    _fields_ = [("grid", GridDescC), ("widths", C.POINTER(C.c_double)), ("obj", ObjectiveC),
+                ("light", LightC), ("want_grad", C.c_int32), ("reserved", C.c_int32),
+                ("design_key", C.c_uint64), ("grad_out", C.POINTER(C.c_double))]
+
+
+class ResultC(C.Structure):
+    _fields_ = [("status", C.c_int32), ("cache_hit", C.c_int32), ("value", C.c_double),
+                ("refine_iters", C.c_int32), ("reserved", C.c_int32),
+                ("rel_residual", C.c_double), ("t_submit_us", C.c_double),
+                ("t_start_us", C.c_double), ("t_end_us", C.c_double),
+                ("footprint", C.c_uint64)]
+
+
+class ServerStatsC(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("submitted", "completed", "failed", "cache_hits",
+                                          "cache_evictions", "admission_waits", "bypasses")] + \
+               [(n, C.c_int32) for n in ("in_flight", "queued", "resident", "reserved")] + \
+               [(n, C.c_uint64) for n in ("arena_bytes", "arena_used", "arena_peak",
+                                          "cache_bytes")]
 
 
 PROFILE_FAMILIES = ["level0", "invert", "gemm", "solve", "residual", "qform", "setup", "grad"]
@@ -60,10 +87,12 @@ class Info:
     ms_factor: float
     ms_solve: float
     ms_qform: float
+    fallback: bool = False
 
     @staticmethod
     def of(c: InfoC) -> "Info":
-        return Info(c.refine_iters, c.rel_residual, c.ms_factor, c.ms_solve, c.ms_qform)
+        return Info(c.refine_iters, c.rel_residual, c.ms_factor, c.ms_solve, c.ms_qform,
+                    bool(c.fallback))
 
 
 class RciError(RuntimeError):
@@ -97,6 +126,12 @@ EXPORTED = {
     "rci_gauss_legendre": (C.c_int, [C.c_int64, C.c_double, C.c_double, _P, _P, _P]),
     "rci_get_eps": (C.c_int, [_P, _P]),
     "rci_apply_operator": (C.c_int, [_P, _P, _P]),
+    "rci_grid_footprint": (C.c_int, [C.POINTER(GridDescC), C.c_int, C.POINTER(C.c_size_t)]),
+    "rci_server_create": (C.c_int, [C.POINTER(ServerDescC), C.POINTER(_P)]),
+    "rci_server_submit": (C.c_int, [_P, C.POINTER(RequestC), C.POINTER(C.c_uint64)]),
+    "rci_server_wait": (C.c_int, [_P, C.c_uint64, C.c_double, C.POINTER(ResultC)]),
+    "rci_server_stats_read": (C.c_int, [_P, C.POINTER(ServerStatsC)]),
+    "rci_server_destroy": (C.c_int, [_P]),
     "rci_profile_enable": (C.c_int, [_P, C.c_int]),
     "rci_profile_read": (C.c_int, [_P, C.POINTER(ProfileC)]),
     "rci_kernel_launches": (C.c_uint64, []),
@@ -358,3 +393,71 @@ def gauss_legendre(n: int, a: float = -1.0, b: float = 1.0, device: int = 0, str
     w = torch.empty_like(x)
     _check(lib().rci_gauss_legendre(n, a, b, _dptr(x), _dptr(w), _stream(stream)))
     return x, w
+
+
+def grid_footprint(desc, prec=None, with_gradient: bool = False) -> int:
+    """Device bytes of a grid for this descriptor (computed on the host)."""
+    by = C.c_size_t()
+    _check(lib().rci_grid_footprint(C.byref(_desc(desc, prec)), 1 if with_gradient else 0,
+                                    C.byref(by)))
+    return by.value
+
+
+class Server:
+    """Continuous-admission evaluation server on one device (see rci_server_* in rci.h).
+
+    submit() returns a ticket at once; wait(ticket) returns the result as a dict (with the
+    gradient as an array for gradient requests)."""
+
+    def __init__(self, device: int = 0, slots: int = 4, arena_bytes: int = 0,
+                 cache_bytes: int = 0, lookahead: int = 4):
+        h = C.c_void_p()
+        d = ServerDescC(device, slots, arena_bytes, cache_bytes, lookahead, 0)
+        _check(lib().rci_server_create(C.byref(d), C.byref(h)))
+        self._h = h
+        self.device = device
+        self._grads = {}
+
+    def submit(self, desc, widths, obj, light, prec=None, want_grad: bool = False,
+               design_key: int = 0) -> int:
+        keep = []
+        w = np.ascontiguousarray(np.asarray(widths, dtype=np.float64))
+        grad = np.empty(w.size) if want_grad else None
+        req = RequestC(_desc(desc, prec, self.device), _hptr(w), _objective(obj, keep),
+                       _light(light, keep), 1 if want_grad else 0, 0, design_key,
+                       _hptr(grad) if grad is not None else None)
+        t = C.c_uint64()
+        _check(lib().rci_server_submit(self._h, C.byref(req), C.byref(t)))
+        self._grads[t.value] = grad      # written by the server before the ticket completes
+        return t.value
+
+    def wait(self, ticket: int, timeout: float = -1.0) -> dict:
+        r = ResultC()
+        _check(lib().rci_server_wait(self._h, ticket, timeout, C.byref(r)))
+        grad = self._grads.pop(ticket, None)
+        return {"status": r.status, "value": r.value, "cache_hit": bool(r.cache_hit),
+                "refine_iters": r.refine_iters, "rel_residual": r.rel_residual,
+                "t_submit_us": r.t_submit_us, "t_start_us": r.t_start_us,
+                "t_end_us": r.t_end_us, "footprint": r.footprint, "grad": grad}
+
+    def stats(self) -> dict:
+        st = ServerStatsC()
+        _check(lib().rci_server_stats_read(self._h, C.byref(st)))
+        return {n: getattr(st, n) for n, _ in ServerStatsC._fields_ if n != "reserved"}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rci_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -140,3 +140,82 @@ def test_design_loop_ascends_within_bounds():
     assert len(h) >= 2 and np.all(np.diff(h) >= 0) and h[-1] > h[0]
     assert F_end == pytest.approx(h[-1], rel=1e-12)
     assert np.all(res.widths >= 0.08) and np.all(res.widths <= 0.36)
+
+
+def _edge_clear(ws, idx, h=0.05, margin=2.5e-4):
+    """Nudge the widths idx so that both edges sit >= margin from every column boundary
+    (then F is smooth in each width over +-margin and central differences apply)."""
+    ws = ws.copy()
+    for m in idx:
+        r = np.mod(ws[m] / 2, h)
+        if r < margin or r > h - margin:
+            ws[m] += 4 * margin
+    return ws
+
+
+@pytest.mark.parametrize("prec", [P.FP32_REFINE, P.FP64])
+def test_gradient_c4_central_differences_on_20_widths(prec):
+    # The gradient workload at full size; central differences with h = 1e-4 wavelengths on
+    # 20 seeded widths, each a fresh set_design + factor + evaluation on the GPU.  Their
+    # O(h^2) truncation error is what separates them from the adjoint gradient: it must
+    # fall fourfold when h is halved, and the Richardson combination of h and h/2 removes it.
+    wl = W.c4_gradient()
+    rng = np.random.default_rng(20)
+    idx = np.sort(rng.choice(wl.grid.n_cells, 20, replace=False))
+    ws = _edge_clear(W.widths(wl.grid.n_cells, 5), idx)
+    with P.Grid(wl.grid, prec=prec) as g:
+        # F to ~1e-13 so that its rounding (/ 2 h) stays far below the truncation error
+        g.set_refinement(1e-13, 30)
+        g.set_design(ws)
+        g.factor()
+        F, grad, _ = g.avg_intensity_grad(wl.objective, wl.light)
+        fd = {}
+        for step in (1e-4, 5e-5):
+            d = np.empty(len(idx))
+            for t, m in enumerate(idx):
+                vals = []
+                for sgn in (1, -1):
+                    w = ws.copy()
+                    w[m] += sgn * step
+                    g.set_design(w)
+                    g.factor()
+                    vals.append(g.avg_intensity(wl.objective, wl.light)[0])
+                d[t] = (vals[0] - vals[1]) / (2 * step)
+            fd[step] = d
+    scale = np.max(np.abs(grad))
+    e1 = np.max(np.abs(fd[1e-4] - grad[idx]))
+    e2 = np.max(np.abs(fd[5e-5] - grad[idx]))
+    rich = (4 * fd[5e-5] - fd[1e-4]) / 3
+    assert e1 <= 3e-5 * scale, (e1, scale)
+    assert 3.5 <= e1 / e2 <= 4.5, (e1, e2)
+    assert np.max(np.abs(rich - grad[idx])) <= 1e-7 * scale
+
+
+def test_gradient_c4_against_oracle_bruteforce_gradient():
+    # full size: the adjoint gradient for the Toeplitz W of a 12-point rule against the
+    # oracle's gradient of the brute-force average over the same 12 angles (the two are
+    # equal up to rounding for a rule symmetric in theta)
+    from oracle.gradient import bruteforce_grad
+    wl = W.c4_gradient()
+    ws = W.widths(wl.grid.n_cells, 9)
+    ev = Evaluation(wl, ws)
+    theta, wq = quadrature_rule(wl.light, 12)
+    F_bf, g_bf = bruteforce_grad(ev, ws, theta, wq)
+    lags = rule_lags(ev.g, theta, wq)
+    with P.Grid(wl.grid, prec=P.FP32_REFINE) as g:
+        g.set_design(ws)
+        g.factor()
+        F, grad, _ = g.avg_intensity_grad(wl.objective, W.Light(W.LIGHT_USER_LAGS, lags=lags))
+    _check(F, grad, F_bf, g_bf, 1e-8)
+
+
+def test_design_loop_c4_100_iterations():
+    # 100 projected-gradient iterations on the full gradient workload, FP32 + refinement
+    wl = W.c4_gradient()
+    ws = W.widths(wl.grid.n_cells, 0)
+    with P.Grid(wl.grid, prec=P.FP32_REFINE) as g:
+        res = optimize(g, wl.objective, wl.light, ws, iters=100, step=0.01)
+    h = np.array(res.history)
+    assert len(res.steps) == 100
+    assert np.all(np.diff(h) >= 0) and h[-1] > h[0], (h[0], h[-1], len(h))
+    assert np.all(res.widths >= 0.08) and np.all(res.widths <= 0.36)

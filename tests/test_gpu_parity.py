@@ -332,3 +332,29 @@ def test_full_size_virtual_focus_properties(maker):
     F_ref = qform_direct(v_src, lags)
     assert abs(F - F_ref) <= 1e-10 * abs(F_ref)
     assert F > 0
+
+
+def test_fp32_grid_falls_back_to_fp64_when_refinement_fails():
+    # zero refinement steps allowed: the FP32 solve alone misses 1e-10, so the grid factors
+    # the design in FP64 and finishes there -- the same numbers as an FP64 grid, bit for bit
+    wl = W.small(kind=W.OBJ_VIRTUAL_FOCUS)
+    ws = _widths(wl, 13)
+    with P.Grid(wl.grid, prec=P.FP64) as g64:
+        g64.set_design(ws)
+        g64.factor()
+        F64, _ = g64.avg_intensity(wl.objective, wl.light)
+    with P.Grid(wl.grid, prec=P.FP32_REFINE) as g:
+        g.set_refinement(1e-10, 0)
+        g.set_design(ws)
+        g.factor()
+        F, info = g.avg_intensity(wl.objective, wl.light)
+        assert info.fallback and F == F64
+        F2, info2 = g.avg_intensity(wl.objective, wl.light)       # stays on the FP64 factor
+        assert info2.fallback and F2 == F64
+        g.set_refinement(1e-10, 30)
+        g.set_design(ws)                                           # a new design: FP32 again
+        g.factor()
+        F3, info3 = g.avg_intensity(wl.objective, wl.light)
+        assert not info3.fallback and abs(F3 - F64) <= 1e-8 * F64
+    F_ref, _ = Evaluation(wl, ws).reciprocal()
+    assert abs(F - F_ref) <= 1e-9 * F_ref

@@ -18,6 +18,12 @@ Workloads (sizes follow the problem statement of each case):
                    50 lambda above the monitor row, light +-20 deg.
   c4_gradient      c2 geometry, virtual focus 20 lambda, light +-15 deg.
   tiny / small     reduced grids for fast tests (thinner PML, fewer rows).
+  serving_requests a stream of requests with Poisson arrivals: width log-uniform in
+                   20..500 lambda (50..1250 cells, ny = 160), concentrator (virtual focus
+                   5..20 lambda up) or collimator (output angle 0..10 deg) half and half,
+                   light a cone (half-angle 5..40 deg) or an annulus (inner 5..20 deg,
+                   outer inner + 5..20 deg) half and half, 30 % also asking for the
+                   gradient.
 """
 from __future__ import annotations
 
@@ -164,6 +170,48 @@ def small(seed: int = 0, n_cells: int = 12, ny: int = 64, kind: int = OBJ_PLANEW
         obj = Objective(kind=OBJ_VIRTUAL_FOCUS, monitor_row=top + 6,
                         x_f=n_cells * g.cell_px / g.ppl / 2, d_rows=40)
     return Workload("small", g, obj, Light(LIGHT_ANNULUS, th1=deg(10), th2=deg(30)), 128, seed)
+
+
+@dataclasses.dataclass
+class Request:
+    arrival_s: float           # seconds after the start of the stream
+    grid: GridDesc
+    widths: np.ndarray
+    objective: Objective
+    light: Light
+    want_grad: bool
+    seed: int
+
+
+def serving_requests(n: int, rate_per_s: float, seed: int = 0, cells=(50, 1250), ny: int = 160,
+                     grad_fraction: float = 0.3, prec: int = PREC_FP32_REFINE) -> list:
+    """n requests with exponential inter-arrival times (mean 1/rate), each a seeded
+    metasurface of its own (design seed = seed * 1_000_003 + k)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    t = 0.0
+    lo, hi = math.log(cells[0]), math.log(cells[1])
+    for k in range(n):
+        t += rng.exponential(1.0 / rate_per_s) if rate_per_s > 0 else 0.0
+        nc = int(round(math.exp(rng.uniform(lo, hi))))
+        g = GridDesc(n_cells=nc, ny=ny, prec=prec)
+        top = _pillar_top(g)
+        if rng.uniform() < 0.5:
+            width = nc * g.cell_px / g.ppl
+            obj = Objective(kind=OBJ_VIRTUAL_FOCUS, monitor_row=top + 10, x_f=width / 2,
+                            d_rows=int(round(rng.uniform(5.0, 20.0) * g.ppl)))
+        else:
+            obj = Objective(kind=OBJ_PLANEWAVE, monitor_row=top + 10,
+                            theta_out=deg(rng.uniform(0.0, 10.0)))
+        if rng.uniform() < 0.5:
+            light = Light(LIGHT_CONE, c=deg(rng.uniform(5.0, 40.0)))
+        else:
+            th1 = rng.uniform(5.0, 20.0)
+            light = Light(LIGHT_ANNULUS, th1=deg(th1), th2=deg(th1 + rng.uniform(5.0, 20.0)))
+        dseed = seed * 1_000_003 + k
+        out.append(Request(t, g, widths(nc, dseed), obj, light,
+                           bool(rng.uniform() < grad_fraction), dseed))
+    return out
 
 
 WORKLOADS = {
