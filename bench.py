@@ -477,7 +477,6 @@ def run_ours(args):
                 "grad_norm_inf": float(np.max(np.abs(grad)))}
             # 100 projected-gradient iterations from seed-0 widths, clamped to [0.08, 0.36]
             from paper_2207_10701_gb300.design import optimize
-            import time
             t0 = time.perf_counter()
             res = optimize(g4, wg.objective, wg.light, W.widths(wg.grid.n_cells, 0), iters=100,
                            step=0.01)
