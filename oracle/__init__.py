@@ -20,6 +20,8 @@ Modules
               FFT and spectral forms of the quadratic form.
   gradient    dF/d(widths) by the adjoint of v^dag W v (Sec. 4.1), the brute-force
               gradient of Eq. 6 angle by angle, and the derivative of the fill raster.
+  correlated  correlated incoherent light (the W of Eq. 3 on a quadrature, the forward
+              double sum of Eq. 5), dense v^dag W v, multi-output objectives (Sec. 6).
 
 Every function is pinned by a ``-m "not gpu"`` test against something other than
 itself (closed forms, library routines used as independent checks, invariants, the
