@@ -83,15 +83,32 @@ __global__ void raster_kernel(GridGeom g, const double* __restrict__ widths,
 // Design-independent part of the stencil, computed once per grid:
 //   dg0 = -s_y/h^2 (1/s_x^{i+1/2} + 1/s_x^{i-1/2}) - s_x/h^2 (1/s_y^{j+1/2} + 1/s_y^{j-1/2}),
 //   kss = k0^2 s_x^i s_y^j,  cx, cy the couplings.
-__global__ void pml_coeff_kernel(GridGeom g, double2* __restrict__ dg0, double2* __restrict__ kss,
-                                 double2* __restrict__ cx, double2* __restrict__ cy) {
+// The stretches depend on one coordinate each, so they are tabulated first (s at the node
+// and 1/s at the half node below it, per column and per row) and combined per point.
+__global__ void pml_tables_kernel(GridGeom g, double2* __restrict__ tx, double2* __restrict__ ty) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t <= g.nx) {
+    tx[2 * t] = t < g.nx ? sx_at(g, t, false) : mkc(0.0, 0.0);
+    tx[2 * t + 1] = crecip(sx_at(g, t, true));
+  }
+  int u = t - (g.nx + 1);
+  if (u >= 0 && u <= g.ny) {
+    ty[2 * u] = u < g.ny ? sy_at(g, u, false) : mkc(0.0, 0.0);
+    ty[2 * u + 1] = crecip(sy_at(g, u, true));
+  }
+}
+
+__global__ void pml_coeff_kernel(GridGeom g, const double2* __restrict__ tx,
+                                 const double2* __restrict__ ty, double2* __restrict__ dg0,
+                                 double2* __restrict__ kss, double2* __restrict__ cx,
+                                 double2* __restrict__ cy) {
   int i = blockIdx.y;
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= g.nx || j >= g.ny) return;
   double h2 = g.h * g.h;
-  double2 sx = sx_at(g, i, false), sy = sy_at(g, j, false);
-  double2 isxm = crecip(sx_at(g, i, true)), isxp = crecip(sx_at(g, i + 1, true));
-  double2 isym = crecip(sy_at(g, j, true)), isyp = crecip(sy_at(g, j + 1, true));
+  double2 sx = tx[2 * i], sy = ty[2 * j];
+  double2 isxm = tx[2 * i + 1], isxp = tx[2 * i + 3];
+  double2 isym = ty[2 * j + 1], isyp = ty[2 * j + 3];
   double2 SYh = (1.0 / h2) * sy, SXh = (1.0 / h2) * sx;
   int64_t k = (int64_t)i * g.ny + j;
   dg0[k] = -(SYh * (isxp + isxm)) - SXh * (isyp + isym);
@@ -277,9 +294,14 @@ cudaError_t launch_raster_eps(const GridGeom& g, const double* widths, double* e
 }
 
 cudaError_t launch_pml_coefficients(const GridGeom& g, double2* dg0, double2* kss, double2* cx,
-                                    double2* cy, cudaStream_t s) {
+                                    double2* cy, double2* scratch, cudaStream_t s) {
+  double2* tx = scratch;                      // 2 (nx + 1) entries
+  double2* ty = scratch + 2 * (g.nx + 1);     // 2 (ny + 1) entries
+  const int nt = g.nx + g.ny + 2;
+  pml_tables_kernel<<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(g, tx, ty); rci_note_launch();
+  RCI_CUDA_TRY(cudaGetLastError());
   dim3 blk(128), grd((unsigned)ceil_div(g.ny, 128), (unsigned)g.nx);
-  pml_coeff_kernel<<<grd, blk, 0, s>>>(g, dg0, kss, cx, cy); rci_note_launch();
+  pml_coeff_kernel<<<grd, blk, 0, s>>>(g, tx, ty, dg0, kss, cx, cy); rci_note_launch();
   return cudaGetLastError();
 }
 

@@ -15,9 +15,10 @@ struct GridGeom {
 cudaError_t launch_raster_eps(const GridGeom& g, const double* widths_dev, double* eps,
                               const double2* dg0, const double2* kss, double2* dg,
                               int32_t* status, cudaStream_t s);
-// once per grid: design-independent stencil parts (PML stretch, couplings)
+// once per grid: design-independent stencil parts (PML stretch, couplings); scratch holds
+// at least 2 (nx + ny + 2) complex entries
 cudaError_t launch_pml_coefficients(const GridGeom& g, double2* dg0, double2* kss, double2* cx,
-                                    double2* cy, cudaStream_t s);
+                                    double2* cy, double2* scratch, cudaStream_t s);
 cudaError_t launch_apply_A(const GridGeom& g, const double2* dg, const double2* cx,
                            const double2* cy, const double2* x, double2* y, int nrhs,
                            cudaStream_t s);
@@ -79,6 +80,19 @@ cudaError_t launch_toeplitz_mv(const double2* v, const double* lags, int64_t n, 
 // out[m] = dF/dw_m = -2 Re sum_c mu_c z_c kss_c d eps_c/d w_m (pillar rows, edge columns)
 cudaError_t launch_width_grad(const GridGeom& g, const double* widths, const double2* mu,
                               const double2* z, const double2* kss, double* out, cudaStream_t s);
+
+// correlated.cu
+// F = sum_{q,q'} om_q om_q' C[q][q'] alpha_q conj(alpha_q'), alpha_q = v^dag b0(theta_q)
+cudaError_t launch_correlated_form(const GridGeom& g, const double2* v, const double* theta,
+                                   const double* om, const double2* C, int nq, double2* alpha,
+                                   double* out, cudaStream_t s);
+// F = Re v^dag W v for a dense row-major W (n x n); part holds n doubles
+cudaError_t launch_dense_form(const double2* v, const double2* W, int64_t n, double* part,
+                              double* out, cudaStream_t s);
+cudaError_t launch_put_column(const double2* b, int64_t N, int ldq, int q, double2* B,
+                              cudaStream_t s);
+cudaError_t launch_gather_source_col(const GridGeom& g, const double2* X, int ldq, int q,
+                                     double2* v, cudaStream_t s);
 
 // qform.cu
 int64_t qform_num_partials(int64_t n);
