@@ -204,6 +204,36 @@ rci_status rci_avg_intensity(rci_grid* g, const rci_objective* obj, const rci_li
 rci_status rci_avg_intensity_grad(rci_grid* g, const rci_objective* obj, const rci_light* light,
                                   double* value, double* dF_dwidths, rci_info* info);
 
+/* Averaged figure of merit for correlated incoherent light (Eq. 5 with Eq. 3): the
+ * angular amplitude correlation <a(theta_q) a*(theta_q')> = C[q][q'] on a quadrature
+ * (theta_q, weight_q = Omega_q) gives the cross-correlation
+ *   W = sum_{q,q'} Omega_q Omega_q' C[q][q'] b0(theta_q) b0(theta_q')^dag
+ * (b0 the unit-power planewave currents of rci_solve_angles), and by Eq. 7
+ *   F = v^dag W v = sum_{q,q'} Omega_q Omega_q' C[q][q'] alpha_q conj(alpha_q'),
+ *   alpha_q = v^dag b0(theta_q),
+ * one reciprocal solve, an nq-point angular transform of v and an nq x nq Hermitian form,
+ * in FP64.  Uncorrelated light is C = diag(rho_q / Omega_q).
+ * theta, weight: HOST float64[nq] (|theta| < pi/2); C: HOST complex128[nq][nq], row-major,
+ * Hermitian; 1 <= nq <= 8192.  out: HOST double. */
+rci_status rci_avg_intensity_correlated(rci_grid* g, const rci_objective* obj, const double* theta,
+                                        const double* weight, int64_t nq, const double* C,
+                                        double* out, rci_info* info);
+
+/* F = v^dag W v (Eq. 7) for a general cross-correlation given as a dense Hermitian matrix
+ * on the source plane: W DEVICE complex128[n_src][n_src], row-major (W[i][l] couples
+ * x_i and x_l, i, l in S), owned by the caller; read once per call.  out: HOST double. */
+rci_status rci_avg_intensity_dense(rci_grid* g, const rci_objective* obj, const double* W,
+                                   double* out, rci_info* info);
+
+/* Several outputs at once (averages over several spots or modes, Sec. 6): for each
+ * objective o, F_o = v_o^dag W v_o with v_o = A^{-dag} w_o, the K reciprocal solves done
+ * as one multi-right-hand-side solve (chunks of 256) on the factorisation.
+ * objs: HOST rci_objective[K], 1 <= K <= 65536.  F_out: HOST float64[K] or NULL;
+ * total: HOST double (sum over the outputs, the trace objective) or NULL. */
+rci_status rci_avg_intensity_multi(rci_grid* g, const rci_objective* objs, int64_t K,
+                                   const rci_light* light, double* F_out, double* total,
+                                   rci_info* info);
+
 /* Brute-force average of Eq. 6 on the same factorisation: for each angle theta_q
  * (measured in the substrate) the equivalent current b0 = sqrt(cos theta) exp(i k_s
  * sin(theta) x_i) on row j_src over S, u_q = A^{-1} b0, f_q = |w^dag u_q|^2, and

@@ -55,6 +55,11 @@ struct rci_grid {
   bool use64 = false;
   double2* corr64 = nullptr;
   int64_t corr64_n = 0;
+  // correlated-light inputs (theta, weights, C, alpha) and multi-output results (grown on demand)
+  void* cbuf = nullptr;
+  size_t cbuf_bytes = 0;
+  double* mF = nullptr;
+  int mF_cap = 0;
   // gradient buffers (allocated by the first gradient call)
   double2 *mu = nullptr, *gsrc = nullptr, *tpart = nullptr;
   double* dgrad = nullptr;
@@ -514,7 +519,7 @@ rci_status rci_destroy_grid(rci_grid* g) {
   void* ps[] = {g->widths, g->eps, g->dg, g->cx, g->cy, g->dg0, g->kss, g->b1, g->x1, g->r1, g->r32, g->d32,
                 g->crow, g->vsrc, g->lags, g->qpart, g->dscal, g->part_r, g->part_b, g->ratio,
                 g->vf_scratch, g->dstatus, g->mb, g->mx, g->mr, g->m32a, g->m32b, g->th_d,
-                g->wq_d, g->f_d, g->mu, g->gsrc, g->tpart, g->dgrad, g->corr64};
+                g->wq_d, g->f_d, g->mu, g->gsrc, g->tpart, g->dgrad, g->corr64, g->cbuf, g->mF};
   for (void* p : ps) dfree(g, p);
   bcr_destroy(g->bcr);
   bcr_destroy(g->bcr64);
@@ -640,7 +645,7 @@ rci_status rci_grid_init(rci_grid* g) {
   DeviceGuard guard(g->device);
   cudaError_t e;
   if ((e = cudaMemsetAsync(g->cx, 0, sizeof(double2) * g->N, g->s)) != cudaSuccess ||
-      (e = launch_pml_coefficients(g->g, g->dg0, g->kss, g->cx, g->cy, g->s)) != cudaSuccess)
+      (e = launch_pml_coefficients(g->g, g->dg0, g->kss, g->cx, g->cy, g->b1, g->s)) != cudaSuccess)
     return cuda_fail(g, e, "grid setup");
   for (auto& ev : g->ev)
     if (!ev && (e = cudaEventCreateWithFlags(&ev, cudaEventDefault)) != cudaSuccess)
@@ -896,6 +901,137 @@ rci_status rci_avg_intensity_grad(rci_grid* g, const rci_objective* obj, const r
     info->ms_factor = ms;
   }
   return s1 != RCI_OK ? s1 : s2;
+}
+
+rci_status rci_avg_intensity_correlated(rci_grid* g, const rci_objective* obj, const double* theta,
+                                        const double* weight, int64_t nq, const double* C,
+                                        double* out, rci_info* info) {
+  if (!g) return RCI_EINVAL;
+  if (!theta || !weight || !C || !out || nq < 1 || nq > 8192)
+    return fail(g, RCI_EINVAL, "bad correlated-light arguments (1 <= nq <= 8192)");
+  for (int64_t q = 0; q < nq; ++q)
+    if (!(std::fabs(theta[q]) < M_PI / 2)) return fail(g, RCI_EINVAL, "angles must lie in (-pi/2, pi/2)");
+  DeviceGuard dg(g->device);
+  const size_t need = sizeof(double) * 2 * nq + sizeof(double2) * (nq * nq + nq) + 256;
+  if (g->cbuf_bytes < need) {
+    dfree(g, g->cbuf);
+    g->cbuf = nullptr;
+    g->cbuf_bytes = 0;
+    CK(dalloc(g, &g->cbuf, need), "correlated-light buffers");
+    g->cbuf_bytes = need;
+  }
+  double* th_d = (double*)g->cbuf;
+  double* om_d = th_d + nq;
+  double2* C_d = (double2*)(((uintptr_t)(om_d + nq) + 15) & ~(uintptr_t)15);
+  double2* al_d = C_d + nq * nq;
+  rci_status sst = reciprocal_solve(g, obj, info);
+  if (sst != RCI_OK && sst != RCI_ENOCONV) return sst;
+  CK(cudaMemcpyAsync(th_d, theta, sizeof(double) * nq, cudaMemcpyHostToDevice, g->s), "angles");
+  CK(cudaMemcpyAsync(om_d, weight, sizeof(double) * nq, cudaMemcpyHostToDevice, g->s), "weights");
+  CK(cudaMemcpyAsync(C_d, C, sizeof(double2) * nq * nq, cudaMemcpyHostToDevice, g->s), "correlation");
+  {
+    const double n = (double)g->g.n_src;
+    ProfScope ps(&g->prof, PF_QFORM, g->s, 8.0 * n * nq + 8.0 * nq * (double)nq,
+                 16.0 * n + 16.0 * nq * (double)nq, 2);
+    CK(launch_correlated_form(g->g, g->vsrc, th_d, om_d, C_d, (int)nq, al_d, g->dscal, g->s),
+       "correlated form");
+  }
+  double F = 0.0;
+  CK(cudaMemcpyAsync(&F, g->dscal, sizeof(double), cudaMemcpyDeviceToHost, g->s), "form copy");
+  CK(cudaStreamSynchronize(g->s), "correlated form");
+  if (g->prof.on) g->prof.collect();
+  if (!std::isfinite(F)) return fail(g, RCI_ENUMERIC, "non-finite averaged intensity");
+  *out = F;
+  return sst;
+}
+
+rci_status rci_avg_intensity_dense(rci_grid* g, const rci_objective* obj, const double* W,
+                                   double* out, rci_info* info) {
+  if (!g) return RCI_EINVAL;
+  if (!W || !out) return fail(g, RCI_EINVAL, "W or out is NULL");
+  DeviceGuard dg(g->device);
+  rci_status sst = reciprocal_solve(g, obj, info);
+  if (sst != RCI_OK && sst != RCI_ENOCONV) return sst;
+  {
+    const double n = (double)g->g.n_src;
+    ProfScope ps(&g->prof, PF_QFORM, g->s, 8.0 * n * n, 16.0 * n * n, 2);
+    // r1 (N complex) is free after the solve: the per-row partials
+    CK(launch_dense_form(g->vsrc, (const double2*)W, g->g.n_src, (double*)g->r1, g->dscal, g->s),
+       "dense form");
+  }
+  double F = 0.0;
+  CK(cudaMemcpyAsync(&F, g->dscal, sizeof(double), cudaMemcpyDeviceToHost, g->s), "form copy");
+  CK(cudaStreamSynchronize(g->s), "dense form");
+  if (g->prof.on) g->prof.collect();
+  if (!std::isfinite(F)) return fail(g, RCI_ENUMERIC, "non-finite averaged intensity");
+  *out = F;
+  return sst;
+}
+
+rci_status rci_avg_intensity_multi(rci_grid* g, const rci_objective* objs, int64_t K,
+                                   const rci_light* light, double* F_out, double* total,
+                                   rci_info* info) {
+  if (!g) return RCI_EINVAL;
+  if (!objs || K < 1 || K > (1 << 16)) return fail(g, RCI_EINVAL, "bad objective list");
+  if (!g->factored) return fail(g, RCI_ESTATE, "grid is not factored");
+  rci_status st = check_light(g, light);
+  if (st != RCI_OK) return st;
+  DeviceGuard dg(g->device);
+  st = ensure_lags(g, light);
+  if (st != RCI_OK) return st;
+  if (g->mF_cap < K) {
+    dfree(g, g->mF);
+    g->mF = nullptr;
+    g->mF_cap = 0;
+    CK(dalloc(g, &g->mF, sizeof(double) * K), "multi-output results");
+    g->mF_cap = (int)K;
+  }
+  const int chunk = K < MAXQ ? (int)K : MAXQ;
+  st = ensure_multi(g, chunk);
+  if (st != RCI_OK) return st;
+  const GridGeom& G = g->g;
+  int worst_it = 0, fb = 0;
+  double worst_res = 0.0;
+  rci_status agg = RCI_OK;
+  for (int64_t o0 = 0; o0 < K; o0 += chunk) {
+    const int c = K - o0 < chunk ? (int)(K - o0) : chunk;
+    // conj(w_o) for the chunk's objectives, one column each
+    for (int q = 0; q < c; ++q) {
+      st = build_objective(g, &objs[o0 + q], g->b1);
+      if (st != RCI_OK) return st;
+      CK(launch_put_column(g->b1, g->N, c, q, g->mb, g->s), "objective column");
+    }
+    rci_info ci{};
+    st = refined_solve(g, g->mb, g->mx, g->mr, g->m32a, g->m32b, c, &ci);
+    if (st != RCI_OK && st != RCI_ENOCONV) return st;
+    if (st == RCI_ENOCONV) agg = st;
+    worst_it = ci.refine_iters > worst_it ? ci.refine_iters : worst_it;
+    worst_res = ci.rel_residual > worst_res ? ci.rel_residual : worst_res;
+    fb |= ci.fallback;
+    for (int q = 0; q < c; ++q) {
+      CK(launch_gather_source_col(G, g->mx, c, q, g->vsrc, g->s), "gather v");
+      const double n = (double)G.n_src;
+      ProfScope ps(&g->prof, PF_QFORM, g->s, 2.0 * n * n, 24.0 * n, 2);
+      CK(launch_qform(g->vsrc, g->lags, G.n_src, g->qpart, g->mF + o0 + q, g->s), "qform");
+    }
+  }
+  std::vector<double> h(K);
+  CK(cudaMemcpyAsync(h.data(), g->mF, sizeof(double) * K, cudaMemcpyDeviceToHost, g->s), "results");
+  CK(cudaStreamSynchronize(g->s), "multi-output");
+  if (g->prof.on) g->prof.collect();
+  double tot = 0.0;
+  for (double x : h) {
+    if (!std::isfinite(x)) return fail(g, RCI_ENUMERIC, "non-finite averaged intensity");
+    tot += x;
+  }
+  if (F_out) std::memcpy(F_out, h.data(), sizeof(double) * K);
+  if (total) *total = tot;
+  if (info) {
+    info->refine_iters = worst_it;
+    info->rel_residual = worst_res;
+    info->fallback = fb;
+  }
+  return agg;
 }
 
 rci_status rci_solve_angles(rci_grid* g, const rci_objective* obj, const double* theta,

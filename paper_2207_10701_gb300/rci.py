@@ -117,6 +117,11 @@ EXPORTED = {
                                     C.POINTER(InfoC)]),
     "rci_avg_intensity_grad": (C.c_int, [_P, C.POINTER(ObjectiveC), C.POINTER(LightC), _D, _D,
                                          C.POINTER(InfoC)]),
+    "rci_avg_intensity_correlated": (C.c_int, [_P, C.POINTER(ObjectiveC), _D, _D, C.c_int64, _D,
+                                               _D, C.POINTER(InfoC)]),
+    "rci_avg_intensity_dense": (C.c_int, [_P, C.POINTER(ObjectiveC), _P, _D, C.POINTER(InfoC)]),
+    "rci_avg_intensity_multi": (C.c_int, [_P, C.POINTER(ObjectiveC), C.c_int64, C.POINTER(LightC),
+                                          _D, _D, C.POINTER(InfoC)]),
     "rci_solve_angles": (C.c_int, [_P, C.POINTER(ObjectiveC), _D, _D, C.c_int64, _D, _D,
                                    C.POINTER(InfoC)]),
     "rci_avg_bruteforce": (C.c_int, [_P, C.POINTER(ObjectiveC), C.POINTER(LightC), C.c_int64,
@@ -317,6 +322,49 @@ class Grid:
         _check(lib().rci_avg_intensity_grad(self._h, C.byref(oc), C.byref(lc), C.byref(out),
                                             _hptr(grad), C.byref(info)), self._h)
         return out.value, grad, Info.of(info)
+
+    def avg_intensity_correlated(self, obj, theta, weight, corr):
+        """F for correlated light: corr[q][q'] = <a(theta_q) a*(theta_q')> on the rule
+        (theta, weight)."""
+        keep = []
+        oc = _objective(obj, keep)
+        th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+        wq = np.ascontiguousarray(np.asarray(weight, dtype=np.float64))
+        cm = np.ascontiguousarray(np.asarray(corr, dtype=np.complex128)).view(np.float64)
+        if cm.size != 2 * th.size * th.size or wq.size != th.size:
+            raise ValueError("corr must be nq x nq and weight nq long")
+        out = C.c_double()
+        info = InfoC()
+        _check(lib().rci_avg_intensity_correlated(self._h, C.byref(oc), _hptr(th), _hptr(wq),
+                                                  th.size, _hptr(cm), C.byref(out),
+                                                  C.byref(info)), self._h)
+        return out.value, Info.of(info)
+
+    def avg_intensity_dense(self, obj, W):
+        """F = v^dag W v for a dense Hermitian W (complex128 CUDA tensor, n_src x n_src)."""
+        torch = _torch()
+        keep = []
+        oc = _objective(obj, keep)
+        Wt = W.to(torch.complex128).contiguous()
+        if Wt.numel() != self.n_src * self.n_src or not Wt.is_cuda:
+            raise ValueError("W must be a CUDA tensor of n_src x n_src entries")
+        out = C.c_double()
+        info = InfoC()
+        _check(lib().rci_avg_intensity_dense(self._h, C.byref(oc), _dptr(Wt), C.byref(out),
+                                             C.byref(info)), self._h)
+        return out.value, Info.of(info)
+
+    def avg_intensity_multi(self, objectives, light):
+        """(F per objective, their sum, Info): one multi-RHS reciprocal solve."""
+        keep = []
+        arr = (ObjectiveC * len(objectives))(*[_objective(o, keep) for o in objectives])
+        lc = _light(light, keep)
+        F = np.empty(len(objectives))
+        tot = C.c_double()
+        info = InfoC()
+        _check(lib().rci_avg_intensity_multi(self._h, arr, len(objectives), C.byref(lc), _hptr(F),
+                                             C.byref(tot), C.byref(info)), self._h)
+        return F, tot.value, Info.of(info)
 
     def solve_angles(self, obj, theta, weight):
         keep = []
