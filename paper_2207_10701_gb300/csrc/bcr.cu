@@ -1223,6 +1223,51 @@ __device__ __forceinline__ void rows_mv(const cplx<T>* __restrict__ M, const cpl
   }
 }
 
+// out[r] = sub[r] - M1[r, :] x1 - M2[r, :] x2 for the RC rows r0 .. r0+RC-1: both
+// matrices' row vectors are loaded before any product, so a block streams its 2 x RC rows
+// in one memory phase (the sums are formed in the order of two rows_mv calls).
+template <typename T, int SMAX>
+__device__ __forceinline__ void rows_mv2(const cplx<T>* __restrict__ M1, const cplx<T>* x1,
+                                         const cplx<T>* __restrict__ M2, const cplx<T>* x2,
+                                         int ny, int r0, cplx<T>* out, const cplx<T>* sub) {
+  using V = typename vec16<T>::type;
+  constexpr int PER = vec16<T>::per;
+  constexpr int RPW = RC / CH_WARPS;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nv = ny / PER;
+  V v1[RPW][SMAX], v2[RPW][SMAX];
+#pragma unroll
+  for (int i = 0; i < RPW; ++i) {
+    const int r = r0 + warp + CH_WARPS * i;
+    const V* A = reinterpret_cast<const V*>(M1 + (int64_t)r * ny);
+    const V* B = reinterpret_cast<const V*>(M2 + (int64_t)r * ny);
+#pragma unroll
+    for (int s = 0; s < SMAX; ++s) {
+      const int q = lane + 32 * s;
+      if (r < ny && q < nv) {
+        v1[i][s] = __ldg(A + q);
+        v2[i][s] = __ldg(B + q);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < RPW; ++i) {
+    const int r = r0 + warp + CH_WARPS * i;
+    cplx<T> a1 = czero<T>(), a2 = czero<T>();
+#pragma unroll
+    for (int s = 0; s < SMAX; ++s) {
+      const int q = lane + 32 * s;
+      if (r < ny && q < nv) {
+        a1 = dot_vec<T>(v1[i][s], x1, PER * q, a1);
+        a2 = dot_vec<T>(v2[i][s], x2, PER * q, a2);
+      }
+    }
+    a1 = warp_sum<T>(a1);
+    a2 = warp_sum<T>(a2);
+    if (lane == 0 && r < ny) out[r] = (sub[r] - a1) - a2;
+  }
+}
+
 // out[c] = sum_a M[a][c] x[a] for the RC columns c0 .. c0+RC-1 (x in shared memory);
 // lanes own columns, warps stride over rows, partial sums reduced through red[CH_WARPS][RC].
 template <typename T>
@@ -1300,12 +1345,18 @@ bwd_chunk_kernel(const cplx<T>* __restrict__ X, const cplx<T>* __restrict__ Y,
     xl[2 * k * ny + c] = xup[k * ny + c];
   __syncthreads();
   if (k >= m) return;
-  // tmp = t - X xa on the chunk rows, then x = tmp - Y xb
-  rows_mv<T, SMAX>(X + k * nn, xa, ny, c0, tmp, t + k * ny);
-  __syncthreads();
-  if (has_b) {
+  // x = (t - X xa) - Y xb on the chunk rows; X and Y rows streamed together where the
+  // register tiles of both fit (FP32 rows up to 192 columns), else one after the other
+  constexpr bool fuse = sizeof(T) == 4 && SMAX <= 6;
+  if (fuse && has_b) {
+    rows_mv2<T, SMAX>(X + k * nn, xa, Y + k * nn, xb, ny, c0, xl + (2 * k + 1) * ny, t + k * ny);
+  } else if (has_b) {
+    rows_mv<T, SMAX>(X + k * nn, xa, ny, c0, tmp, t + k * ny);
+    __syncthreads();
     rows_mv<T, SMAX>(Y + k * nn, xb, ny, c0, xl + (2 * k + 1) * ny, tmp);
   } else {
+    rows_mv<T, SMAX>(X + k * nn, xa, ny, c0, tmp, t + k * ny);
+    __syncthreads();
     for (int c = c0 + threadIdx.x; c < c0 + RC && c < ny; c += CH_THREADS)
       xl[(2 * k + 1) * ny + c] = tmp[c];
   }
