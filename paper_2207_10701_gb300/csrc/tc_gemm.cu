@@ -14,8 +14,8 @@
 //
 // Tiling: one CTA per 128 x 80 complex output tile (M = 128 rows, N = 160 real columns
 // per MMA); K in chunks of 8 complex (16 real) per pipeline stage, 3 stages (two CTAs per SM).  All 256
-// threads stage operands (global -> registers -> split -> shared memory in the
-// K-major, no-swizzle core-matrix layout); thread 0 issues the MMAs for a stage and
+// threads stage operands (global -> registers, issued 3 stages ahead -> split -> shared
+// memory in the K-major, no-swizzle core-matrix layout); thread 0 issues the MMAs for a stage and
 // commits them to that stage's mbarrier, which releases the buffer for reuse.  The
 // accumulator lives in tensor memory (160 of 256 allocated columns) and is read back by
 // the 8 warps (warp w: lanes 32 (w % 4).., columns half (w / 4)).
@@ -219,84 +219,89 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_cgemm_kernel(TcArgs p) {
           bv[r][c] = TB ? B[(int64_t)gj * p.ldb + gk] : B[(int64_t)gk * p.ldb + gj];
       }
   };
-  float2 av[2][2], bv[2][2], av_next[2][2], bv_next[2][2];
-  if (nkb > 0) load_stage(0, av, bv);
+  // Operand loads run PF stages ahead through a ring of register sets (static indices: the
+  // K loop is unrolled by the ring length), so their latency overlaps PF stages of work.
+  constexpr int PF = 3, RING = PF + 1;
+  float2 av[RING][2][2], bv[RING][2][2];
+#pragma unroll
+  for (int d = 0; d < PF; ++d)
+    if (d < nkb) load_stage(d, av[d], bv[d]);
   bool ok = true;
-  for (int kb = 0; kb < nkb; ++kb) {
-    const int st = kb % NSTAGE;
-    unsigned char* sb = stages + (size_t)st * STAGE_BYTES;
-    // issue the next stage's global loads before anything waits
-    if (kb + 1 < nkb) load_stage(kb + 1, av_next, bv_next);
-    if (kb >= NSTAGE) {
-      // the MMAs that last read this buffer must have completed
-      if (!mbar_wait(&mbar[st], (uint32_t)((kb / NSTAGE - 1) & 1))) ok = false;
-    }
-    if (__syncthreads_or(!ok)) {
-      ok = false;
-      break;
-    }
-    unsigned char* a_hi = sb;
-    unsigned char* a_lo = sb + A_BYTES;
-    unsigned char* b_hi = sb + 2 * A_BYTES;
-    unsigned char* b_lo = sb + 2 * A_BYTES + B_BYTES;
-    // ---- A tile: rows i0 .. i0+127, complex k0 .. k0+7: row am, real k 4 apa .. 4 apa + 3
+  int committed = -1;  // last stage whose MMAs thread 0 committed (uniform across the CTA)
+  for (int base = 0; base < nkb && ok; base += RING) {
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      float h[4], l[4];
-      split_tf32(av[q][0].x, h[0], l[0]);
-      split_tf32(av[q][0].y, h[1], l[1]);
-      split_tf32(av[q][1].x, h[2], l[2]);
-      split_tf32(av[q][1].y, h[3], l[3]);
-      const uint32_t o = core_off(am[q], 4 * apa[q]);
-      *reinterpret_cast<float4*>(a_hi + o) = make_float4(h[0], h[1], h[2], h[3]);
-      *reinterpret_cast<float4*>(a_lo + o) = make_float4(l[0], l[1], l[2], l[3]);
-    }
-    // ---- B tile: complex k0 .. k0+7, complex columns j0 .. j0+79.  Each complex b
-    // expands into the real block [[br, bi], [-bi, br]] at (k', n') = (2k.., 2n..), stored
-    // K-major (element (n', k')): row 2n gets (br, -bi), row 2n+1 gets (bi, br) per k.
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      if (!bval[r]) continue;
-      float rh0, rl0, ih0, il0, rh1, rl1, ih1, il1;
-      split_tf32(bv[r][0].x, rh0, rl0);
-      split_tf32(bv[r][0].y, ih0, il0);
-      split_tf32(bv[r][1].x, rh1, rl1);
-      split_tf32(bv[r][1].y, ih1, il1);
-      const uint32_t o = core_off(2 * bn[r], 4 * bpb[r]);
-      *reinterpret_cast<float4*>(b_hi + o) = make_float4(rh0, -ih0, rh1, -ih1);
-      *reinterpret_cast<float4*>(b_hi + o + 16u) = make_float4(ih0, rh0, ih1, rh1);
-      *reinterpret_cast<float4*>(b_lo + o) = make_float4(rl0, -il0, rl1, -il1);
-      *reinterpret_cast<float4*>(b_lo + o + 16u) = make_float4(il0, rl0, il1, rl1);
-    }
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      av[q][0] = av_next[q][0];
-      av[q][1] = av_next[q][1];
-      bv[q][0] = bv_next[q][0];
-      bv[q][1] = bv_next[q][1];
-    }
-    // make the generic-proxy shared-memory writes visible to the tensor cores
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo);
-      const uint32_t bh = smem_u32(b_hi), bl = smem_u32(b_lo);
-#pragma unroll
-      for (int ks = 0; ks < KR / 8; ++ks) {
-        const uint32_t off = (uint32_t)ks * 2 * LBO;  // 8 real k = two core matrices
-        mma_tf32(tmem, smem_desc(ah + off), smem_desc(bh + off), (kb | ks) ? 1u : 0u);
-        mma_tf32(tmem, smem_desc(ah + off), smem_desc(bl + off), 1u);
-        mma_tf32(tmem, smem_desc(al + off), smem_desc(bh + off), 1u);
+    for (int g = 0; g < RING; ++g) {
+      const int kb = base + g;
+      if (kb >= nkb || !ok) break;
+      const int st = kb % NSTAGE;
+      unsigned char* sb = stages + (size_t)st * STAGE_BYTES;
+      if (kb + PF < nkb) load_stage(kb + PF, av[(g + PF) % RING], bv[(g + PF) % RING]);
+      if (kb >= NSTAGE) {
+        // the MMAs that last read this buffer must have completed
+        if (!mbar_wait(&mbar[st], (uint32_t)((kb / NSTAGE - 1) & 1))) ok = false;
       }
-      mma_commit(&mbar[st]);
+      if (__syncthreads_or(!ok)) {
+        ok = false;
+        break;
+      }
+      unsigned char* a_hi = sb;
+      unsigned char* a_lo = sb + A_BYTES;
+      unsigned char* b_hi = sb + 2 * A_BYTES;
+      unsigned char* b_lo = sb + 2 * A_BYTES + B_BYTES;
+      // ---- A tile: rows i0 .. i0+127, complex k0 .. k0+7: row am, real k 4 apa .. 4 apa + 3
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        float h[4], l[4];
+        split_tf32(av[g][q][0].x, h[0], l[0]);
+        split_tf32(av[g][q][0].y, h[1], l[1]);
+        split_tf32(av[g][q][1].x, h[2], l[2]);
+        split_tf32(av[g][q][1].y, h[3], l[3]);
+        const uint32_t o = core_off(am[q], 4 * apa[q]);
+        *reinterpret_cast<float4*>(a_hi + o) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4*>(a_lo + o) = make_float4(l[0], l[1], l[2], l[3]);
+      }
+      // ---- B tile: complex k0 .. k0+7, complex columns j0 .. j0+79.  Each complex b
+      // expands into the real block [[br, bi], [-bi, br]] at (k', n') = (2k.., 2n..), stored
+      // K-major (element (n', k')): row 2n gets (br, -bi), row 2n+1 gets (bi, br) per k.
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        if (!bval[r]) continue;
+        float rh0, rl0, ih0, il0, rh1, rl1, ih1, il1;
+        split_tf32(bv[g][r][0].x, rh0, rl0);
+        split_tf32(bv[g][r][0].y, ih0, il0);
+        split_tf32(bv[g][r][1].x, rh1, rl1);
+        split_tf32(bv[g][r][1].y, ih1, il1);
+        const uint32_t o = core_off(2 * bn[r], 4 * bpb[r]);
+        *reinterpret_cast<float4*>(b_hi + o) = make_float4(rh0, -ih0, rh1, -ih1);
+        *reinterpret_cast<float4*>(b_hi + o + 16u) = make_float4(ih0, rh0, ih1, rh1);
+        *reinterpret_cast<float4*>(b_lo + o) = make_float4(rl0, -il0, rl1, -il1);
+        *reinterpret_cast<float4*>(b_lo + o + 16u) = make_float4(il0, rl0, il1, rl1);
+      }
+      // make the generic-proxy shared-memory writes visible to the tensor cores
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo);
+        const uint32_t bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+#pragma unroll
+        for (int ks = 0; ks < KR / 8; ++ks) {
+          const uint32_t off = (uint32_t)ks * 2 * LBO;  // 8 real k = two core matrices
+          mma_tf32(tmem, smem_desc(ah + off), smem_desc(bh + off), (kb | ks) ? 1u : 0u);
+          mma_tf32(tmem, smem_desc(ah + off), smem_desc(bl + off), 1u);
+          mma_tf32(tmem, smem_desc(al + off), smem_desc(bh + off), 1u);
+        }
+        mma_commit(&mbar[st]);
+      }
+      committed = kb;
     }
   }
-  // ---- all MMAs done
-  if (ok && nkb > 0) {
-    const int last = nkb - 1;
-    if (!mbar_wait(&mbar[last % NSTAGE], (uint32_t)((last / NSTAGE) & 1))) ok = false;
+  // ---- all committed MMAs done (also after a timeout, before the tensor memory is freed);
+  // a commit tracks every earlier MMA of the issuing thread
+  if (committed >= 0) {
+    if (!mbar_wait(&mbar[committed % NSTAGE], (uint32_t)((committed / NSTAGE) & 1))) ok = false;
   }
+  if (committed != nkb - 1) ok = false;
   ok = !__syncthreads_or(!ok);
   if (!ok) {
     if (tid == 0) atomicCAS(p.status, DEV_OK, DEV_TIMEOUT);
