@@ -42,6 +42,9 @@ constexpr uint32_t B_BYTES = TNR * KR * 4;       // one split of the B tile
 constexpr uint32_t STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr size_t SMEM_BYTES = (size_t)NSTAGE * STAGE_BYTES + 1024;
 constexpr long long WAIT_LIMIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+constexpr int EP_LD = TNR + 1;                   // epilogue tile row stride (floats)
+static_assert((size_t)TM * EP_LD * 4 <= (size_t)NSTAGE * STAGE_BYTES,
+              "the epilogue tile reuses the stage buffers");
 
 struct TcArgs {
   int M, N, K;
@@ -306,29 +309,38 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_cgemm_kernel(TcArgs p) {
   if (!ok) {
     if (tid == 0) atomicCAS(p.status, DEV_OK, DEV_TIMEOUT);
   } else {
+    // Epilogue through shared memory (the stage buffers are free once every MMA is done):
+    // warp w copies TMEM lanes 32 (w % 4).. (tile rows), column half w / 4, into a
+    // row-major tile padded to EP_LD floats per row, so both this copy (a row per lane) and
+    // the read below (consecutive columns per lane) are free of bank conflicts; then each
+    // warp combines and stores rows of C with consecutive complex columns across lanes.
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    float* tile = reinterpret_cast<float*>(stages);
+    const int lane = tid & 31;
     const int lane_base = 32 * (warp & 3);
     const int col_half = warp >> 2;  // real columns [80 col_half, 80 col_half + 80)
-    const int row = lane_base + (tid & 31);
-    const int gi = i0 + row;
-    float2* C = p.C + z * p.sC;
-    const float2* C0 = p.C0 ? p.C0 + z * p.sC0 : nullptr;
+    const int row = lane_base + lane;
 #pragma unroll
     for (int c = 0; c < TNR / 2 / 16; ++c) {
       const int col = col_half * (TNR / 2) + 16 * c;
       float v[16];
       tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)col, v);
-      if (gi < p.M) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int gj = j0 + col / 2 + q;
-          if (gj < p.N) {
-            float2 acc = make_float2(v[2 * q], v[2 * q + 1]);
-            float2 r = p.alpha * acc;
-            if (C0) r = cfma(p.beta, C0[(int64_t)gi * p.ldc0 + gj], r);
-            C[(int64_t)gi * p.ldc + gj] = r;
-          }
-        }
+      for (int q = 0; q < 16; ++q) tile[row * EP_LD + col + q] = v[q];
+    }
+    __syncthreads();
+    float2* C = p.C + z * p.sC;
+    const float2* C0 = p.C0 ? p.C0 + z * p.sC0 : nullptr;
+    for (int r = warp; r < TM; r += TC_THREADS / 32) {
+      const int gi = i0 + r;
+      if (gi >= p.M) break;
+      for (int q = lane; q < TNC; q += 32) {
+        const int gj = j0 + q;
+        if (gj >= p.N) break;
+        const float2 acc = make_float2(tile[r * EP_LD + 2 * q], tile[r * EP_LD + 2 * q + 1]);
+        float2 res = p.alpha * acc;
+        if (C0) res = cfma(p.beta, C0[(int64_t)gi * p.ldc0 + gj], res);
+        C[(int64_t)gi * p.ldc + gj] = res;
       }
     }
   }
