@@ -354,6 +354,240 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_cgemm_kernel(TcArgs p) {
   }
 }
 
+// ---------------------------------------------------------------- stacked form
+// For real alpha and beta, the complex product as the real product of the stacked
+//   A_s = [[Ar, -Ai], [Ai, Ar]]  (2M x 2K: the pairs (ar, -ai) per complex k on the rows of
+//   the top half, (ai, ar) on the bottom half)   and   B_s = [Br; Bi]  (2K x N, (br, bi) per k),
+// so C_s = A_s B_s holds Re C in its first M rows and Im C in the next M.  One 128-row tile
+// of C_s covers 160 complex columns, and 2M = 320 rows fill three tiles where the
+// expanded-B form needs four 128 x 80 tiles for a 160 x 160 product; B is staged as it is
+// stored (one 16-byte core row per pair of complex k instead of two).
+constexpr int TNS = 160;                          // complex (= real) columns per CTA
+constexpr uint32_t BS_BYTES = TNS * KR * 4;       // one split of the B_s tile
+constexpr uint32_t SSTAGE_BYTES = 2 * A_BYTES + 2 * BS_BYTES;
+constexpr size_t SSMEM_BYTES = (size_t)NSTAGE * SSTAGE_BYTES + 1024;
+constexpr uint32_t IDESC_S = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TNS >> 3) << 17) |
+                             ((uint32_t)(TM >> 4) << 24);
+constexpr int SB_ITEMS = (TNS * (KC / 2) + TC_THREADS - 1) / TC_THREADS;  // 3
+constexpr int EPS_LD = TNS + 1;
+static_assert((size_t)TM * EPS_LD * 4 <= (size_t)NSTAGE * SSTAGE_BYTES,
+              "the epilogue tile reuses the stage buffers");
+
+__device__ __forceinline__ void mma_tf32_s(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                           uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(IDESC_S), "r"(accumulate));
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(TC_THREADS, 2) tc_cgemm_stacked_kernel(TcArgs p) {
+  extern __shared__ __align__(1024) unsigned char sm_raw[];
+  unsigned char* stages = sm_raw;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm_raw + (size_t)NSTAGE * SSTAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + NSTAGE);
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t z = blockIdx.z;
+  const float2* A = p.A + z * p.sA;
+  const float2* B = p.B + z * p.sB;
+  const int R0 = blockIdx.y * TM, j0 = blockIdx.x * TNS;
+
+  if (tid == 0) {
+    for (int s = 0; s < NSTAGE; ++s) mbar_init(&mbar[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  const int nkb = (p.K + KC - 1) / KC;
+  // A_s items: 128 rows x 4 pairs of complex k, 2 per thread (row am, pair apa); row
+  // R0 + am of A_s is row ar of A, in the top half (Re) or the bottom half (Im).
+  int am[2], apa[2], ar[2];
+  bool atop[2], aval[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    if (!TA) {
+      const int e = tid * 2 + q;
+      am[q] = e >> 2;
+      apa[q] = e & 3;
+    } else {
+      const int e = tid + TC_THREADS * q;
+      am[q] = e & (TM - 1);
+      apa[q] = e >> 7;
+    }
+    const int R = R0 + am[q];
+    atop[q] = R < p.M;
+    ar[q] = atop[q] ? R : R - p.M;
+    aval[q] = R < 2 * p.M;
+  }
+  // B_s items: 160 columns x 4 pairs, up to 3 per thread (column bn, pair bpb)
+  int bn[SB_ITEMS], bpb[SB_ITEMS];
+  bool bval[SB_ITEMS];
+#pragma unroll
+  for (int r = 0; r < SB_ITEMS; ++r) {
+    const int e = tid + TC_THREADS * r;
+    bval[r] = e < TNS * (KC / 2);
+    if (!TB) {
+      bn[r] = e % TNS;
+      bpb[r] = e / TNS;
+    } else {
+      bpb[r] = e & 3;
+      bn[r] = e >> 2;
+    }
+  }
+  auto load_stage = [&](int kb, float2 (&av)[2][2], float2 (&bv)[SB_ITEMS][2]) {
+    const int k0 = kb * KC;
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int gk = k0 + 2 * apa[q] + c;
+        av[q][c] = make_float2(0.f, 0.f);
+        if (aval[q] && gk < p.K)
+          av[q][c] = TA ? A[(int64_t)gk * p.lda + ar[q]] : A[(int64_t)ar[q] * p.lda + gk];
+      }
+#pragma unroll
+    for (int r = 0; r < SB_ITEMS; ++r)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int gk = k0 + 2 * bpb[r] + c, gj = j0 + bn[r];
+        bv[r][c] = make_float2(0.f, 0.f);
+        if (bval[r] && gk < p.K && gj < p.N)
+          bv[r][c] = TB ? B[(int64_t)gj * p.ldb + gk] : B[(int64_t)gk * p.ldb + gj];
+      }
+  };
+  constexpr int PF = 2, RING = PF + 1;
+  float2 av[RING][2][2], bv[RING][SB_ITEMS][2];
+#pragma unroll
+  for (int d = 0; d < PF; ++d)
+    if (d < nkb) load_stage(d, av[d], bv[d]);
+  bool ok = true;
+  int committed = -1;
+  for (int base = 0; base < nkb && ok; base += RING) {
+#pragma unroll
+    for (int g = 0; g < RING; ++g) {
+      const int kb = base + g;
+      if (kb >= nkb || !ok) break;
+      const int st = kb % NSTAGE;
+      unsigned char* sb = stages + (size_t)st * SSTAGE_BYTES;
+      if (kb + PF < nkb) load_stage(kb + PF, av[(g + PF) % RING], bv[(g + PF) % RING]);
+      if (kb >= NSTAGE) {
+        if (!mbar_wait(&mbar[st], (uint32_t)((kb / NSTAGE - 1) & 1))) ok = false;
+      }
+      if (__syncthreads_or(!ok)) {
+        ok = false;
+        break;
+      }
+      unsigned char* a_hi = sb;
+      unsigned char* a_lo = sb + A_BYTES;
+      unsigned char* b_hi = sb + 2 * A_BYTES;
+      unsigned char* b_lo = sb + 2 * A_BYTES + BS_BYTES;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float2 a0 = av[g][q][0], a1 = av[g][q][1];
+        // top half: (ar, -ai) per complex k; bottom half: (ai, ar)
+        const float x0 = atop[q] ? a0.x : a0.y, x1 = atop[q] ? -a0.y : a0.x;
+        const float x2 = atop[q] ? a1.x : a1.y, x3 = atop[q] ? -a1.y : a1.x;
+        float h[4], l[4];
+        split_tf32(x0, h[0], l[0]);
+        split_tf32(x1, h[1], l[1]);
+        split_tf32(x2, h[2], l[2]);
+        split_tf32(x3, h[3], l[3]);
+        const uint32_t o = core_off(am[q], 4 * apa[q]);
+        *reinterpret_cast<float4*>(a_hi + o) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4*>(a_lo + o) = make_float4(l[0], l[1], l[2], l[3]);
+      }
+#pragma unroll
+      for (int r = 0; r < SB_ITEMS; ++r) {
+        if (!bval[r]) continue;
+        float h[4], l[4];
+        split_tf32(bv[g][r][0].x, h[0], l[0]);
+        split_tf32(bv[g][r][0].y, h[1], l[1]);
+        split_tf32(bv[g][r][1].x, h[2], l[2]);
+        split_tf32(bv[g][r][1].y, h[3], l[3]);
+        const uint32_t o = core_off(bn[r], 4 * bpb[r]);
+        *reinterpret_cast<float4*>(b_hi + o) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4*>(b_lo + o) = make_float4(l[0], l[1], l[2], l[3]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo);
+        const uint32_t bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+#pragma unroll
+        for (int ks = 0; ks < KR / 8; ++ks) {
+          const uint32_t off = (uint32_t)ks * 2 * LBO;
+          mma_tf32_s(tmem, smem_desc(ah + off), smem_desc(bh + off), (kb | ks) ? 1u : 0u);
+          mma_tf32_s(tmem, smem_desc(ah + off), smem_desc(bl + off), 1u);
+          mma_tf32_s(tmem, smem_desc(al + off), smem_desc(bh + off), 1u);
+        }
+        mma_commit(&mbar[st]);
+      }
+      committed = kb;
+    }
+  }
+  if (committed >= 0) {
+    if (!mbar_wait(&mbar[committed % NSTAGE], (uint32_t)((committed / NSTAGE) & 1))) ok = false;
+  }
+  if (committed != nkb - 1) ok = false;
+  ok = !__syncthreads_or(!ok);
+  if (!ok) {
+    if (tid == 0) atomicCAS(p.status, DEV_OK, DEV_TIMEOUT);
+  } else {
+    // epilogue through shared memory, as in tc_cgemm_kernel: tile rows are Re rows (top
+    // half) or Im rows (bottom half) of C, tile columns complex columns
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    float* tile = reinterpret_cast<float*>(stages);
+    const int lane = tid & 31;
+    const int lane_base = 32 * (warp & 3);
+    const int col_half = warp >> 2;
+    const int row = lane_base + lane;
+#pragma unroll
+    for (int c = 0; c < TNS / 2 / 16; ++c) {
+      const int col = col_half * (TNS / 2) + 16 * c;
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)col, v);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) tile[row * EPS_LD + col + q] = v[q];
+    }
+    __syncthreads();
+    float* C = reinterpret_cast<float*>(p.C + z * p.sC);
+    const float* C0 = p.C0 ? reinterpret_cast<const float*>(p.C0 + z * p.sC0) : nullptr;
+    for (int r = warp; r < TM; r += TC_THREADS / 32) {
+      const int R = R0 + r;
+      if (R >= 2 * p.M) break;
+      const int gi = R < p.M ? R : R - p.M, comp = R < p.M ? 0 : 1;
+      for (int q = lane; q < TNS; q += 32) {
+        const int gj = j0 + q;
+        if (gj >= p.N) break;
+        float res = p.alpha.x * tile[r * EPS_LD + q];
+        if (C0) res = fmaf(p.beta.x, C0[2 * ((int64_t)gi * p.ldc0 + gj) + comp], res);
+        C[2 * ((int64_t)gi * p.ldc + gj) + comp] = res;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_tc_cgemm(int M, int N, int K, bool ta, bool tb, float2 alpha, const float2* A,
@@ -371,6 +605,20 @@ cudaError_t launch_tc_cgemm(int M, int N, int K, bool ta, bool tb, float2 alpha,
     rci_note_launch();
     return cudaGetLastError();
   };
+  if (N <= TNS && alpha.y == 0.f && beta.y == 0.f) {  // real scalars: the stacked form
+    dim3 gs(1, (unsigned)ceil_div(2 * (int64_t)M, TM), (unsigned)batch);
+    auto launch_s = [&](auto kern) -> cudaError_t {
+      RCI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)SSMEM_BYTES));
+      kern<<<gs, TC_THREADS, SSMEM_BYTES, s>>>(a);
+      rci_note_launch();
+      return cudaGetLastError();
+    };
+    if (!ta && !tb) return launch_s(tc_cgemm_stacked_kernel<false, false>);
+    if (!ta && tb) return launch_s(tc_cgemm_stacked_kernel<false, true>);
+    if (ta && !tb) return launch_s(tc_cgemm_stacked_kernel<true, false>);
+    return launch_s(tc_cgemm_stacked_kernel<true, true>);
+  }
   if (!ta && !tb) return launch(tc_cgemm_kernel<false, false>);
   if (!ta && tb) return launch(tc_cgemm_kernel<false, true>);
   if (ta && !tb) return launch(tc_cgemm_kernel<true, false>);
