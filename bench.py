@@ -587,7 +587,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--other-steps", type=int, default=5)
-    ap.add_argument("--streams", type=int, default=3,
+    ap.add_argument("--streams", type=int, default=4,
                     help="independent evaluations in flight (one stream + host thread each)")
     ap.add_argument("--quick", action="store_true", help="skip the FP64 / brute-force extras")
     ap.add_argument("--no-cpu-baseline", action="store_true")
