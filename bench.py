@@ -119,13 +119,26 @@ def _barrier(ws):
 
 
 def _max_over_ranks(x: float, ws: int) -> float:
+    """The largest x over the ranks (the slowest rank's time sets a replica run's value)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def _replica_seeds(rank: int, n: int) -> list:
+    """Design seeds of one replica: disjoint across ranks, so every rank evaluates its own
+    designs (replicas only: no data is exchanged between ranks)."""
+    return [rank * 1_000_000 + s for s in range(n)]
+
+
+def _replica_value(ws: int, steps: int, slowest_ms: float) -> float:
+    """Whole-job evaluations per second: all ranks' evaluations over the slowest rank's time."""
+    return ws * steps / (slowest_ms * 1e-3)
 
 
 # DRAM bytes (read + write) per ny x ny block inverted by the FP32 register-panel Gauss-Jordan
@@ -268,7 +281,7 @@ def run_ours(args):
     prec = P.FP64 if args.prec == "fp64" else P.FP32_REFINE
     nc = wl.grid.n_cells
     K, Wm, S = args.steps, args.warmup, max(1, args.streams)
-    seeds = [rank * 1_000_000 + s for s in range(K + Wm)]
+    seeds = _replica_seeds(rank, K + Wm)
     widths_dev = torch.tensor(np.stack([W.widths(nc, s) for s in seeds]), dtype=torch.float64,
                               device=f"cuda:{local}")
     # S independent evaluators, one stream and one host thread each (evaluations of
@@ -331,7 +344,7 @@ def run_ours(args):
     launches = P.kernel_launches() - l0
     clk = clocks.stop()
     total_ms = _max_over_ranks(total_ms, ws_)
-    value = ws_ * K / (total_ms * 1e-3)
+    value = _replica_value(ws_, K, total_ms)
 
     # ---- one evaluation with nothing else in flight (first evaluator): its latency, and
     # the per-kernel-family device times (CUDA events around each family inside the
