@@ -498,6 +498,34 @@ def run_ours(args):
                 "F_start": res.history[0], "F_end": res.history[-1],
                 "gain": round(res.history[-1] / res.history[0], 4),
                 "seconds": round(time.perf_counter() - t0, 2)}
+        # the precision form at 1000 wavelengths (2500 cells, nx 20040, ny 224, 4.5M unknowns,
+        # virtual focus 50 wavelengths up, cone of +-20 degrees): cold FP32 + refinement
+        # evaluations against the FP64 form of the same design, one grid at a time
+        w3 = W.c3_precision()
+        ws3 = W.widths(w3.grid.n_cells, 0)
+        c3 = {"workload": w3.name}
+        for pr, name, reps in ((P.FP32_REFINE, "fp32_refine", 2), (P.FP64, "fp64", 1)):
+            with P.Grid(w3.grid, prec=pr, device=local, stream=stream) as g5:
+                c3["unknowns"] = g5.N
+                t = []
+                for k in range(reps + (1 if pr == P.FP32_REFINE else 0)):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    g5.set_design(ws3)
+                    g5.factor()
+                    F3, info3 = g5.avg_intensity(w3.objective, w3.light)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    if k or pr == P.FP64:
+                        t.append(e0.elapsed_time(e1))
+                c3[name] = {"ms_per_eval": round(sum(t) / len(t), 2), "F": F3,
+                            "refine_iters": info3.refine_iters,
+                            "rel_residual": info3.rel_residual, "fp64_fallback": info3.fallback,
+                            "device_gb": round(g5.device_bytes() / 1e9, 2)}
+        c3["rel_diff_fp32_refine_vs_fp64"] = (abs(c3["fp32_refine"]["F"] - c3["fp64"]["F"])
+                                              / abs(c3["fp64"]["F"]))
+        extra["c3_precision"] = c3
         line.update(extra)
     if rank == 0 and not args.no_cpu_baseline and ws_ == 1:
         line["cpu_baseline"] = _cpu_baseline()
