@@ -500,13 +500,23 @@ __device__ __forceinline__ bool gj_pivot(const cplx<T> (&x)[R], int k, int n, in
       }
     }
   }
+  if constexpr (sizeof(T) == 4) {
+    // |re| + |im| >= 0, so its bit pattern orders like the value: the largest key over the
+    // warp, then the lowest row holding it (a lane without rows has key 0 and row k, which
+    // changes nothing: row k itself is a candidate whenever the maximum is 0)
+    const uint32_t key = best >= T(0) ? __float_as_uint(best) : 0u;
+    const uint32_t kmax = __reduce_max_sync(0xffffffffu, key);
+    bi = (int)__reduce_min_sync(0xffffffffu, key == kmax ? (uint32_t)bi : 0xffffffffu);
+    best = __uint_as_float(kmax);
+  } else {
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    T ob = __shfl_xor_sync(0xffffffffu, best, off);
-    int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-    if (ob > best || (ob == best && oi < bi)) {
-      best = ob;
-      bi = oi;
+    for (int off = 16; off > 0; off >>= 1) {
+      T ob = __shfl_xor_sync(0xffffffffu, best, off);
+      int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
     }
   }
   const int p = bi;
@@ -1301,6 +1311,53 @@ __device__ __forceinline__ void cols_mvT(const cplx<T>* __restrict__ M, const cp
   __syncthreads();
 }
 
+// outP[c] = sum_a X[a][c] x[a] and, if Y, outQ[c] = sum_a Y[a][c] x[a], for the RC columns
+// c0 .. c0+RC-1, the loads of both matrices in one loop (the sums are formed in the order of
+// two cols_mvT calls); red holds 2 x CH_WARPS x RC entries.
+template <typename T>
+__device__ __forceinline__ void cols_mvT2(const cplx<T>* __restrict__ X,
+                                          const cplx<T>* __restrict__ Y, const cplx<T>* x, int ny,
+                                          int c0, cplx<T>* red, cplx<T>* outP, cplx<T>* outQ) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = c0 + lane;
+  cplx<T> ap = czero<T>(), aq = czero<T>();
+  constexpr int U = 5;
+  for (int a0 = warp; a0 < ny; a0 += CH_WARPS * U) {
+    cplx<T> mx[U], my[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int a = a0 + CH_WARPS * u;
+      const bool v = a < ny && c < ny;
+      mx[u] = v ? __ldg(X + (int64_t)a * ny + c) : czero<T>();
+      my[u] = (v && Y) ? __ldg(Y + (int64_t)a * ny + c) : czero<T>();
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int a = a0 + CH_WARPS * u;
+      if (a < ny) {
+        ap = cfma(mx[u], x[a], ap);
+        aq = cfma(my[u], x[a], aq);
+      }
+    }
+  }
+  red[warp * RC + lane] = ap;
+  red[(CH_WARPS + warp) * RC + lane] = aq;
+  __syncthreads();
+  if (warp == 0) {
+    cplx<T> sp = czero<T>(), sq = czero<T>();
+#pragma unroll
+    for (int w = 0; w < CH_WARPS; ++w) {
+      sp = sp + red[w * RC + lane];
+      sq = sq + red[(CH_WARPS + w) * RC + lane];
+    }
+    if (c < ny) {
+      outP[c] = sp;
+      if (Y) outQ[c] = sq;
+    }
+  }
+  __syncthreads();
+}
+
 // Dense level, forward: t_k = Dinv_k b_{2k+1} (rows of chunk), P_k = X_k^T b_{2k+1},
 // Q_k = Y_k^T b_{2k+1} (columns of chunk).  Grid (m, ceil(ny / RC)).
 template <typename T, int SMAX>
@@ -1318,8 +1375,9 @@ fwd_chunk_kernel(const cplx<T>* __restrict__ Dinv, const cplx<T>* __restrict__ X
   for (int c = threadIdx.x; c < ny; c += CH_THREADS) bs[c] = B[(2 * k + 1) * ny + c];
   __syncthreads();
   rows_mv<T, SMAX>(Dinv + k * nn, bs, ny, c0, t + k * ny, nullptr);
-  cols_mvT<T>(X + k * nn, bs, ny, c0, red, P + k * ny);
-  if (2 * k + 2 < n) cols_mvT<T>(Y + k * nn, bs, ny, c0, red, Q + k * ny);
+  // X^T b and Y^T b on the chunk columns, both matrices streamed together
+  cols_mvT2<T>(X + k * nn, 2 * k + 2 < n ? Y + k * nn : nullptr, bs, ny, c0, red, P + k * ny,
+               Q + k * ny);
 }
 
 // Dense level, backward: x_l[2k] = x_up[k];
@@ -1668,7 +1726,7 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
       return cudaErrorInvalidValue;  // (grid creation keeps ny within these limits)
     const int smax = (int)ceil_div(ny, 32 * vec16<T>::per);
     const unsigned nch = (unsigned)ceil_div(ny, RC);
-    const size_t red_smem = (size_t)CH_WARPS * RC * sizeof(cplx<T>);
+    const size_t red_smem = (size_t)2 * CH_WARPS * RC * sizeof(cplx<T>);
 #define RCI_SMAX_DISPATCH(KERNEL, GRID, SMEM, ...)                                   \
   do {                                                                               \
     switch (smax) {                                                                  \
