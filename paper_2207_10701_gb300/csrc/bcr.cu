@@ -682,6 +682,251 @@ gj_regpanel_kernel(cplx<T>* __restrict__ src, int64_t src_stride, cplx<T>* __res
     for (int jx = tid; jx < n; jx += NT) o[i * n + jx] = a[i * n + idx[jx]];
 }
 
+// Look-ahead variant for FP32 blocks held in shared memory (n <= 160), 1024 threads in
+// two groups of 16 warps.  While the panel group factors panel P+1 (the register-panel
+// steps above, one named barrier per pivot), the trailing group applies the rank-nb
+// update of panel P to every column outside panels P and P+1; the panel group has
+// applied that update to its own columns first.  The matrix row stride is odd (n | 1
+// entries), so that a warp reading one column (rows lane, lane + 32, ...) meets no bank
+// conflict.  Every entry is formed by the same operations in the same order as in
+// gj_regpanel_kernel, so the two give identical results.
+constexpr int GJLA_THREADS = 1024, GJLA_NB = 16, GJLA_R = 5, GJLA_TR = 5, GJLA_TC = 2;
+
+struct GjLaSmem {
+  // byte offsets for an n x n complex-FP32 matrix (odd row stride n | 1)
+  size_t cb0, cb1, tpanel, perm, idx, mat, total;
+  __host__ __device__ GjLaSmem(int n) {
+    const size_t e = sizeof(float2);
+    const size_t tmax = (size_t)GJLA_NB * (n > GJLA_NB ? n - GJLA_NB : 1);
+    cb0 = 0;
+    cb1 = cb0 + (size_t)n * e;
+    tpanel = cb1 + (size_t)n * e;
+    perm = tpanel + tmax * e;
+    idx = perm + (size_t)n * sizeof(int);
+    mat = (idx + (size_t)n * sizeof(int) + 15) & ~(size_t)15;
+    total = mat + (size_t)n * (n | 1) * e;
+  }
+};
+
+__device__ __forceinline__ void group_bar(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(GJLA_THREADS / 2) : "memory");
+}
+
+// Panel group: Gauss-Jordan steps on columns c0 .. c0+nb-1, warp t holding column c0 + t
+// in x (rows lane + 32 r); the columns are written back to the matrix at the end.
+__device__ __forceinline__ void gjla_panel(float2 (&x)[GJLA_R], int c0, int nb, int n, int ld,
+                                           float2* a, float2* cbuf0, float2* cbuf1, int* s_p,
+                                           float2* s_pinv, int* perm, int* s_sing) {
+  constexpr int R = GJLA_R;
+  const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
+  if (t == 0 && !gj_pivot<float, R>(x, c0, n, lane, cbuf0, &s_p[0], &s_pinv[0], perm))
+    *s_sing = 1;
+  group_bar(1);
+  for (int kt = 0; kt < nb; ++kt) {
+    const int k = c0 + kt, b = kt & 1;
+    if (t < nb) {
+      const int p = s_p[b];
+      const float2 pinv = s_pinv[b];
+      const float2* colk = b ? cbuf1 : cbuf0;
+      const float2 vp = warp_row<float, R>(x, p), vk = warp_row<float, R>(x, k);
+      const float2 rk = (t == kt ? mkc(1.f, 0.f) : vp) * pinv;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int i = lane + 32 * r;
+        if (i < n) {
+          const float2 old = i == k ? vp : (i == p ? vk : x[r]);
+          const float2 base = t == kt ? czero<float>() : old;
+          x[r] = i == k ? rk : cfms(colk[i], rk, base);
+        }
+      }
+      if (t == kt + 1 &&
+          !gj_pivot<float, R>(x, k + 1, n, lane, b ? cbuf0 : cbuf1, &s_p[b ^ 1], &s_pinv[b ^ 1],
+                              perm))
+        *s_sing = 1;
+    }
+    group_bar(1);
+  }
+  if (t < nb) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i = lane + 32 * r;
+      if (i < n) a[i * ld + c0 + t] = x[r];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(GJLA_THREADS)
+gj_lookahead_kernel(const float2* __restrict__ src, int64_t src_stride, float2* __restrict__ out,
+                    int64_t out_stride, int n, int32_t* status) {
+  constexpr int R = GJLA_R, NB = GJLA_NB, TR = GJLA_TR, TC = GJLA_TC, TY = 16;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const GjLaSmem L(n);
+  float2* const cbuf0 = reinterpret_cast<float2*>(sm_raw + L.cb0);
+  float2* const cbuf1 = reinterpret_cast<float2*>(sm_raw + L.cb1);
+  float2* const tp = reinterpret_cast<float2*>(sm_raw + L.tpanel);
+  int* const perm = reinterpret_cast<int*>(sm_raw + L.perm);
+  int* const idx = reinterpret_cast<int*>(sm_raw + L.idx);
+  float2* const a = reinterpret_cast<float2*>(sm_raw + L.mat);
+  __shared__ int s_p[2];
+  __shared__ float2 s_pinv[2];
+  __shared__ int s_sing;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ld = n | 1;
+  const bool panel_group = warp < 16;
+  const float2* g = src + (int64_t)blockIdx.x * src_stride;
+  if (tid == 0) s_sing = 0;
+  for (int e = tid; e < n * n; e += GJLA_THREADS) {
+    const int i = e / n, j = e - i * n;
+    a[i * ld + j] = g[e];
+  }
+  __syncthreads();
+  float2 x[R];
+  if (panel_group) {
+    const int nb0 = n < NB ? n : NB;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i = lane + 32 * r;
+      x[r] = (warp < nb0 && i < n) ? a[i * ld + warp] : czero<float>();
+    }
+    gjla_panel(x, 0, nb0, n, ld, a, cbuf0, cbuf1, s_p, s_pinv, perm, &s_sing);
+  }
+  __syncthreads();
+  for (int c0 = 0; c0 < n; c0 += NB) {
+    const int nb = n - c0 < NB ? n - c0 : NB;
+    const int c1 = c0 + nb;                                 // next panel
+    const int nb1 = n - c1 < NB ? n - c1 : NB;              // its width (0: none)
+    if (n - nb == 0) break;
+    if (panel_group) {
+      if (nb1 > 0) {
+        const int j = c1 + warp;
+        if (warp < nb1) {
+          // this column: row swaps of panel P (in order), then the rank-nb update of P
+          if (lane == 0)
+            for (int u = 0; u < nb; ++u) {
+              const int rr = c0 + u, p = perm[rr];
+              if (p != rr) {
+                const float2 y = a[rr * ld + j];
+                a[rr * ld + j] = a[p * ld + j];
+                a[p * ld + j] = y;
+              }
+            }
+          __syncwarp();
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int i = lane + 32 * r;
+            const bool prow = i >= c0 && i < c1;
+            x[r] = (i < n && !prow) ? a[i * ld + j] : czero<float>();
+          }
+          for (int u = 0; u < nb; ++u) {
+            const float2 tv = a[(c0 + u) * ld + j];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              const int i = lane + 32 * r;
+              if (i < n) x[r] = cfma(a[i * ld + c0 + u], tv, x[r]);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) x[r] = czero<float>();
+        }
+        gjla_panel(x, c1, nb1, n, ld, a, cbuf0, cbuf1, s_p, s_pinv, perm, &s_sing);
+      }
+    } else {
+      // trailing group: columns q = 0 .. mt-1, matrix column jc(q), outside panels P, P+1
+      const int tt = tid - GJLA_THREADS / 2, ty = warp - 16, tx = lane;
+      const int mt = n - nb - nb1;
+      for (int q = tt; q < mt; q += GJLA_THREADS / 2) {
+        const int jc = q < c0 ? q : q + nb + nb1;
+        for (int u = 0; u < nb; ++u) {
+          const int rr = c0 + u, p = perm[rr];
+          if (p != rr) {
+            const float2 y = a[rr * ld + jc];
+            a[rr * ld + jc] = a[p * ld + jc];
+            a[p * ld + jc] = y;
+          }
+        }
+      }
+      group_bar(2);
+      for (int u = 0; u < nb; ++u)
+        for (int q = tt; q < mt; q += GJLA_THREADS / 2) {
+          const int jc = q < c0 ? q : q + nb + nb1;
+          tp[u * mt + q] = a[(c0 + u) * ld + jc];
+        }
+      group_bar(2);
+      for (int r0 = 0; r0 < n; r0 += TY * TR) {
+        for (int q0 = 0; q0 < mt; q0 += 32 * TC) {
+          float2 acc[TR][TC];
+#pragma unroll
+          for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int c = 0; c < TC; ++c) {
+              const int i = r0 + ty + TY * r, q = q0 + tx + 32 * c;
+              const int jc = q < c0 ? q : q + nb + nb1;
+              const bool prow = i >= c0 && i < c1;
+              acc[r][c] = (i < n && q < mt && !prow) ? a[i * ld + jc] : czero<float>();
+            }
+          for (int u = 0; u < nb; ++u) {
+            float2 zv[TR], tv[TC];
+#pragma unroll
+            for (int r = 0; r < TR; ++r) {
+              const int i = r0 + ty + TY * r;
+              zv[r] = i < n ? a[i * ld + c0 + u] : czero<float>();
+            }
+#pragma unroll
+            for (int c = 0; c < TC; ++c) {
+              const int q = q0 + tx + 32 * c;
+              tv[c] = q < mt ? tp[u * mt + q] : czero<float>();
+            }
+#pragma unroll
+            for (int r = 0; r < TR; ++r)
+#pragma unroll
+              for (int c = 0; c < TC; ++c) acc[r][c] = cfma(zv[r], tv[c], acc[r][c]);
+          }
+#pragma unroll
+          for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int c = 0; c < TC; ++c) {
+              const int i = r0 + ty + TY * r, q = q0 + tx + 32 * c;
+              const int jc = q < c0 ? q : q + nb + nb1;
+              if (i < n && q < mt) a[i * ld + jc] = acc[r][c];
+            }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    for (int jx = 0; jx < n; ++jx) idx[jx] = jx;
+    for (int k = n - 1; k >= 0; --k) {
+      const int p = perm[k];
+      const int y = idx[k];
+      idx[k] = idx[p];
+      idx[p] = y;
+    }
+    if (s_sing) atomicCAS(status, DEV_OK, DEV_SINGULAR);
+  }
+  __syncthreads();
+  float2* o = out + (int64_t)blockIdx.x * out_stride;
+  for (int e = tid; e < n * n; e += GJLA_THREADS) {
+    const int i = e / n, jx = e - i * n;
+    o[e] = a[i * ld + idx[jx]];
+  }
+}
+
+cudaError_t launch_gj_lookahead(const float2* src, int64_t src_stride, float2* out,
+                                int64_t out_stride, int n, int batch, int32_t* status,
+                                cudaStream_t s) {
+  const GjLaSmem L(n);
+  if (L.total > SMEM_LIMIT || n > 32 * GJLA_R) return cudaErrorInvalidValue;
+  if (L.total > 48 * 1024)
+    RCI_CUDA_TRY(cudaFuncSetAttribute(gj_lookahead_kernel,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+  gj_lookahead_kernel<<<batch, GJLA_THREADS, L.total, s>>>(src, src_stride, out, out_stride, n,
+                                                           status);
+  rci_note_launch();
+  return cudaGetLastError();
+}
+
 template <typename T, bool SMEM, int R, int TR, int TC, int NT>
 cudaError_t launch_gj_reg(cplx<T>* src, int64_t src_stride, cplx<T>* out, int64_t out_stride,
                           int n, int batch, int32_t* status, cudaStream_t s) {
@@ -716,6 +961,8 @@ cudaError_t launch_gj(cplx<T>* src, int64_t src_stride, cplx<T>* out, int64_t ou
   if (batch <= 0) return cudaSuccess;
   if (n > 1024) return cudaErrorInvalidValue;
   if constexpr (sizeof(T) == 4) {
+    if (n <= 160 && GjLaSmem(n).total <= SMEM_LIMIT)
+      return launch_gj_lookahead(src, src_stride, out, out_stride, n, batch, status, s);
     if (n <= 160 && GjSmem<T>(n, 16, true).total <= SMEM_LIMIT)
       return launch_gj_reg<T, true, 5, 5, 5, 512>(src, src_stride, out, out_stride, n, batch,
                                                   status, s);
