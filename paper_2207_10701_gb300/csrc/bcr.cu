@@ -683,27 +683,31 @@ gj_regpanel_kernel(cplx<T>* __restrict__ src, int64_t src_stride, cplx<T>* __res
 }
 
 // Look-ahead variant for FP32 blocks held in shared memory (n <= 160), 1024 threads in
-// two groups of 16 warps.  While the panel group factors panel P+1 (the register-panel
-// steps above, one named barrier per pivot), the trailing group applies the rank-nb
-// update of panel P to every column outside panels P and P+1; the panel group has
-// applied that update to its own columns first.  The matrix row stride is odd (n | 1
-// entries), so that a warp reading one column (rows lane, lane + 32, ...) meets no bank
-// conflict.  Every entry is formed by the same operations in the same order as in
-// gj_regpanel_kernel, so the two give identical results.
+// two groups of 16 warps.  While the panel group factors panel P+1 (one named barrier per
+// pivot), the trailing group applies the rank-nb update of panel P to every column outside
+// panels P and P+1; the panel group has applied that update to its own columns first.
+// Rows are never swapped: the pivot of column k is physical row piv[k], chosen among the
+// rows not yet used as pivots, and the permutations are applied when the inverse is
+// written out (inverse[i][j] = M[piv[i]][pinv[j]] for the in-place result M).  Every entry
+// is formed by the same operations as with explicit swaps, so the result equals that of
+// gj_regpanel_kernel whenever no two pivot candidates tie.  The matrix row stride is odd
+// (n | 1 entries), so that a warp reading one column (rows lane, lane + 32, ...) meets no
+// bank conflict.
 constexpr int GJLA_THREADS = 1024, GJLA_NB = 16, GJLA_R = 5, GJLA_TR = 5, GJLA_TC = 2;
 
 struct GjLaSmem {
   // byte offsets for an n x n complex-FP32 matrix (odd row stride n | 1)
-  size_t cb0, cb1, tpanel, perm, idx, mat, total;
+  size_t cb0, cb1, tpanel, piv, rowpanel, pinv, mat, total;
   __host__ __device__ GjLaSmem(int n) {
     const size_t e = sizeof(float2);
     const size_t tmax = (size_t)GJLA_NB * (n > GJLA_NB ? n - GJLA_NB : 1);
     cb0 = 0;
     cb1 = cb0 + (size_t)n * e;
     tpanel = cb1 + (size_t)n * e;
-    perm = tpanel + tmax * e;
-    idx = perm + (size_t)n * sizeof(int);
-    mat = (idx + (size_t)n * sizeof(int) + 15) & ~(size_t)15;
+    piv = tpanel + tmax * e;
+    rowpanel = piv + (size_t)n * sizeof(int);
+    pinv = rowpanel + (size_t)n * sizeof(int);
+    mat = (pinv + (size_t)n * sizeof(int) + 15) & ~(size_t)15;
     total = mat + (size_t)n * (n | 1) * e;
   }
 };
@@ -712,36 +716,88 @@ __device__ __forceinline__ void group_bar(int id) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(GJLA_THREADS / 2) : "memory");
 }
 
+// Pivot of column k held by this warp (rows lane + 32 r, `used` marks rows already taken):
+// the largest |re| + |im| among unused rows, ties to the lowest row; publishes the column,
+// the row, 1/pivot, piv[k] and rowpanel[row] = c0.  Returns false if the column is zero
+// on every unused row (or holds no number there).
+__device__ __forceinline__ bool gjla_pivot(const float2 (&x)[GJLA_R], unsigned used, int k,
+                                           int c0, int n, int lane, float2* colk, int* s_p,
+                                           float2* s_pinv, int* piv, int* rowpanel) {
+  constexpr int R = GJLA_R;
+  float best = -1.f;
+  int bi = 0x7fffffff, first = 0x7fffffff;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = lane + 32 * r;
+    if (i < n) {
+      colk[i] = x[r];
+      if (!((used >> r) & 1u)) {
+        const float v = cabs1(x[r]);
+        if (first == 0x7fffffff) first = i;
+        if (v > best) {
+          best = v;
+          bi = i;
+        }
+      }
+    }
+  }
+  // |re| + |im| >= 0 orders like its bit pattern: the largest key over the warp, then the
+  // lowest row holding it; a lane without a candidate offers key 0 and its first unused row
+  if (best < 0.f) bi = first;
+  const uint32_t key = best >= 0.f ? __float_as_uint(best) : 0u;
+  const uint32_t kmax = __reduce_max_sync(0xffffffffu, key);
+  const int p = (int)__reduce_min_sync(0xffffffffu, key == kmax ? (uint32_t)bi : 0xffffffffu);
+  const float2 vp = warp_row<float, R>(x, p);
+  if (lane == 0) {
+    *s_p = p;
+    *s_pinv = crecip(vp);
+    piv[k] = p;
+    rowpanel[p] = c0;
+  }
+  return __uint_as_float(kmax) > 0.f;
+}
+
 // Panel group: Gauss-Jordan steps on columns c0 .. c0+nb-1, warp t holding column c0 + t
 // in x (rows lane + 32 r); the columns are written back to the matrix at the end.
 __device__ __forceinline__ void gjla_panel(float2 (&x)[GJLA_R], int c0, int nb, int n, int ld,
                                            float2* a, float2* cbuf0, float2* cbuf1, int* s_p,
-                                           float2* s_pinv, int* perm, int* s_sing) {
+                                           float2* s_pinv, int* piv, int* rowpanel, int* s_sing) {
   constexpr int R = GJLA_R;
   const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
-  if (t == 0 && !gj_pivot<float, R>(x, c0, n, lane, cbuf0, &s_p[0], &s_pinv[0], perm))
+  unsigned used = 0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = lane + 32 * r;
+    if (i >= n || rowpanel[i] >= 0) used |= 1u << r;
+  }
+  if (t == 0 && !gjla_pivot(x, used, c0, c0, n, lane, cbuf0, &s_p[0], &s_pinv[0], piv, rowpanel))
     *s_sing = 1;
   group_bar(1);
   for (int kt = 0; kt < nb; ++kt) {
-    const int k = c0 + kt, b = kt & 1;
+    const int b = kt & 1;
     if (t < nb) {
       const int p = s_p[b];
       const float2 pinv = s_pinv[b];
       const float2* colk = b ? cbuf1 : cbuf0;
-      const float2 vp = warp_row<float, R>(x, p), vk = warp_row<float, R>(x, k);
-      const float2 rk = (t == kt ? mkc(1.f, 0.f) : vp) * pinv;
+      if (lane == (p & 31)) used |= 1u << (p >> 5);
+      if (t == kt) {
+        // the pivot column becomes -column / pivot, and 1 / pivot on the pivot row
+        const float2 rk = mkc(1.f, 0.f) * pinv;
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int i = lane + 32 * r;
-        if (i < n) {
-          const float2 old = i == k ? vp : (i == p ? vk : x[r]);
-          const float2 base = t == kt ? czero<float>() : old;
-          x[r] = i == k ? rk : cfms(colk[i], rk, base);
+        for (int r = 0; r < R; ++r) {
+          const int i = lane + 32 * r;
+          if (i < n) x[r] = i == p ? rk : cfms(colk[i], rk, czero<float>());
+        }
+      } else {
+        const float2 rk = warp_row<float, R>(x, p) * pinv;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int i = lane + 32 * r;
+          if (i < n) x[r] = i == p ? rk : cfms(colk[i], rk, x[r]);
         }
       }
-      if (t == kt + 1 &&
-          !gj_pivot<float, R>(x, k + 1, n, lane, b ? cbuf0 : cbuf1, &s_p[b ^ 1], &s_pinv[b ^ 1],
-                              perm))
+      if (t == kt + 1 && !gjla_pivot(x, used, c0 + kt + 1, c0, n, lane, b ? cbuf0 : cbuf1,
+                                     &s_p[b ^ 1], &s_pinv[b ^ 1], piv, rowpanel))
         *s_sing = 1;
     }
     group_bar(1);
@@ -764,8 +820,13 @@ gj_lookahead_kernel(const float2* __restrict__ src, int64_t src_stride, float2* 
   float2* const cbuf0 = reinterpret_cast<float2*>(sm_raw + L.cb0);
   float2* const cbuf1 = reinterpret_cast<float2*>(sm_raw + L.cb1);
   float2* const tp = reinterpret_cast<float2*>(sm_raw + L.tpanel);
-  int* const perm = reinterpret_cast<int*>(sm_raw + L.perm);
-  int* const idx = reinterpret_cast<int*>(sm_raw + L.idx);
+  int* const piv = reinterpret_cast<int*>(sm_raw + L.piv);
+  // panel start at which the row became a pivot, -1 before: the trailing group reads it for
+  // the rows of panel P while the panel group sets it for rows of panel P+1 (from -1 to
+  // c0 + nb); either value differs from c0 of panel P, so the reading does not depend on
+  // the order
+  int* const rowpanel = reinterpret_cast<int*>(sm_raw + L.rowpanel);
+  int* const pinv = reinterpret_cast<int*>(sm_raw + L.pinv);
   float2* const a = reinterpret_cast<float2*>(sm_raw + L.mat);
   __shared__ int s_p[2];
   __shared__ float2 s_pinv[2];
@@ -775,6 +836,7 @@ gj_lookahead_kernel(const float2* __restrict__ src, int64_t src_stride, float2* 
   const bool panel_group = warp < 16;
   const float2* g = src + (int64_t)blockIdx.x * src_stride;
   if (tid == 0) s_sing = 0;
+  for (int i = tid; i < n; i += GJLA_THREADS) rowpanel[i] = -1;
   for (int e = tid; e < n * n; e += GJLA_THREADS) {
     const int i = e / n, j = e - i * n;
     a[i * ld + j] = g[e];
@@ -788,7 +850,7 @@ gj_lookahead_kernel(const float2* __restrict__ src, int64_t src_stride, float2* 
       const int i = lane + 32 * r;
       x[r] = (warp < nb0 && i < n) ? a[i * ld + warp] : czero<float>();
     }
-    gjla_panel(x, 0, nb0, n, ld, a, cbuf0, cbuf1, s_p, s_pinv, perm, &s_sing);
+    gjla_panel(x, 0, nb0, n, ld, a, cbuf0, cbuf1, s_p, s_pinv, piv, rowpanel, &s_sing);
   }
   __syncthreads();
   for (int c0 = 0; c0 < n; c0 += NB) {
@@ -800,25 +862,14 @@ gj_lookahead_kernel(const float2* __restrict__ src, int64_t src_stride, float2* 
       if (nb1 > 0) {
         const int j = c1 + warp;
         if (warp < nb1) {
-          // this column: row swaps of panel P (in order), then the rank-nb update of P
-          if (lane == 0)
-            for (int u = 0; u < nb; ++u) {
-              const int rr = c0 + u, p = perm[rr];
-              if (p != rr) {
-                const float2 y = a[rr * ld + j];
-                a[rr * ld + j] = a[p * ld + j];
-                a[p * ld + j] = y;
-              }
-            }
-          __syncwarp();
+          // this column: the rank-nb update of panel P (its pivot rows start from zero)
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const int i = lane + 32 * r;
-            const bool prow = i >= c0 && i < c1;
-            x[r] = (i < n && !prow) ? a[i * ld + j] : czero<float>();
+            x[r] = (i < n && rowpanel[i] != c0) ? a[i * ld + j] : czero<float>();
           }
           for (int u = 0; u < nb; ++u) {
-            const float2 tv = a[(c0 + u) * ld + j];
+            const float2 tv = a[piv[c0 + u] * ld + j];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
               const int i = lane + 32 * r;
@@ -829,31 +880,27 @@ gj_lookahead_kernel(const float2* __restrict__ src, int64_t src_stride, float2* 
 #pragma unroll
           for (int r = 0; r < R; ++r) x[r] = czero<float>();
         }
-        gjla_panel(x, c1, nb1, n, ld, a, cbuf0, cbuf1, s_p, s_pinv, perm, &s_sing);
+        gjla_panel(x, c1, nb1, n, ld, a, cbuf0, cbuf1, s_p, s_pinv, piv, rowpanel, &s_sing);
       }
     } else {
       // trailing group: columns q = 0 .. mt-1, matrix column jc(q), outside panels P, P+1
       const int tt = tid - GJLA_THREADS / 2, ty = warp - 16, tx = lane;
       const int mt = n - nb - nb1;
-      for (int q = tt; q < mt; q += GJLA_THREADS / 2) {
-        const int jc = q < c0 ? q : q + nb + nb1;
-        for (int u = 0; u < nb; ++u) {
-          const int rr = c0 + u, p = perm[rr];
-          if (p != rr) {
-            const float2 y = a[rr * ld + jc];
-            a[rr * ld + jc] = a[p * ld + jc];
-            a[p * ld + jc] = y;
-          }
+      for (int u = 0; u < nb; ++u) {
+        const int pr = piv[c0 + u];
+        for (int q = tt; q < mt; q += GJLA_THREADS / 2) {
+          const int jc = q < c0 ? q : q + nb + nb1;
+          tp[u * mt + q] = a[pr * ld + jc];
         }
       }
       group_bar(2);
-      for (int u = 0; u < nb; ++u)
-        for (int q = tt; q < mt; q += GJLA_THREADS / 2) {
-          const int jc = q < c0 ? q : q + nb + nb1;
-          tp[u * mt + q] = a[(c0 + u) * ld + jc];
-        }
-      group_bar(2);
       for (int r0 = 0; r0 < n; r0 += TY * TR) {
+        bool prow[TR];
+#pragma unroll
+        for (int r = 0; r < TR; ++r) {
+          const int i = r0 + ty + TY * r;
+          prow[r] = i < n && rowpanel[i] == c0;
+        }
         for (int q0 = 0; q0 < mt; q0 += 32 * TC) {
           float2 acc[TR][TC];
 #pragma unroll
@@ -862,8 +909,7 @@ gj_lookahead_kernel(const float2* __restrict__ src, int64_t src_stride, float2* 
             for (int c = 0; c < TC; ++c) {
               const int i = r0 + ty + TY * r, q = q0 + tx + 32 * c;
               const int jc = q < c0 ? q : q + nb + nb1;
-              const bool prow = i >= c0 && i < c1;
-              acc[r][c] = (i < n && q < mt && !prow) ? a[i * ld + jc] : czero<float>();
+              acc[r][c] = (i < n && q < mt && !prow[r]) ? a[i * ld + jc] : czero<float>();
             }
           for (int u = 0; u < nb; ++u) {
             float2 zv[TR], tv[TC];
@@ -895,21 +941,13 @@ gj_lookahead_kernel(const float2* __restrict__ src, int64_t src_stride, float2* 
     }
     __syncthreads();
   }
-  if (tid == 0) {
-    for (int jx = 0; jx < n; ++jx) idx[jx] = jx;
-    for (int k = n - 1; k >= 0; --k) {
-      const int p = perm[k];
-      const int y = idx[k];
-      idx[k] = idx[p];
-      idx[p] = y;
-    }
-    if (s_sing) atomicCAS(status, DEV_OK, DEV_SINGULAR);
-  }
+  for (int l = tid; l < n; l += GJLA_THREADS) pinv[piv[l]] = l;
+  if (tid == 0 && s_sing) atomicCAS(status, DEV_OK, DEV_SINGULAR);
   __syncthreads();
   float2* o = out + (int64_t)blockIdx.x * out_stride;
   for (int e = tid; e < n * n; e += GJLA_THREADS) {
     const int i = e / n, jx = e - i * n;
-    o[e] = a[i * ld + idx[jx]];
+    o[e] = a[piv[i] * ld + pinv[jx]];
   }
 }
 
