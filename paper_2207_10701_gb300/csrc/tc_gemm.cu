@@ -690,6 +690,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_cgemm_ws_kernel(TcArgs p) {
       const int tile = (int)blockIdx.x + tl * (int)gridDim.x;
       const int z = tile / mt;
       const int Rw = (tile - z * mt) * TM + 32 * ew;           // first row of this warp
+      const bool uniform = Rw + 32 <= p.M || Rw >= p.M;
+      const int gi0 = Rw < p.M ? Rw : Rw - p.M, comp0 = Rw < p.M ? 0 : 1;
+      const int nval = 2 * p.M - Rw;                           // rows of C_s left (<= 0: none)
       float* C = reinterpret_cast<float*>(p.C + (int64_t)z * p.sC);
       const float* C0 = p.C0 ? reinterpret_cast<const float*>(p.C0 + (int64_t)z * p.sC0) : nullptr;
       for (int c = 0; c < TNS / WS_EPI_CH; ++c) {
@@ -703,32 +706,51 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_cgemm_ws_kernel(TcArgs p) {
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           mbar_arrive(&accempty[b]);
         }
-        // lane = column gj of the chunk; every C0 value is loaded before the first store
-        // (C may be C0, so the loads could not move past the stores)
-        const int gj = c * WS_EPI_CH + lane;
-        float c0v[32];
-        if (C0) {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const int R = Rw + i;
-            const int gi = R < p.M ? R : R - p.M, comp = R < p.M ? 0 : 1;
-            c0v[i] = (R < 2 * p.M && gj < p.N) ? C0[2 * ((int64_t)gi * p.ldc0 + gj) + comp] : 0.f;
-          }
-        }
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           wt[lane * WS_EPI_LD + q] = v[q];
           wt[lane * WS_EPI_LD + 16 + q] = w[q];
         }
         __syncwarp();
+        // lane = column gj of the chunk, rows Rw + i; every C0 value is loaded before the
+        // first store (C may be C0, so the loads could not move past the stores)
+        const int gj = c * WS_EPI_CH + lane;
+        float c0v[32];
+        if (uniform) {
+          // the warp's rows are all Re rows or all Im rows of C: one row pointer
+          if (gj < p.N) {
+            if (C0) {
+              const float* q0 = C0 + 2 * ((int64_t)gi0 * p.ldc0 + gj) + comp0;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int R = Rw + i;
-          const int gi = R < p.M ? R : R - p.M, comp = R < p.M ? 0 : 1;
-          if (R < 2 * p.M && gj < p.N) {
-            float res = p.alpha.x * wt[i * WS_EPI_LD + lane];
-            if (C0) res = fmaf(p.beta.x, c0v[i], res);
-            C[2 * ((int64_t)gi * p.ldc + gj) + comp] = res;
+              for (int i = 0; i < 32; ++i) c0v[i] = i < nval ? q0[(int64_t)i * 2 * p.ldc0] : 0.f;
+            }
+            float* q = C + 2 * ((int64_t)gi0 * p.ldc + gj) + comp0;
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (i < nval) {
+                float res = p.alpha.x * wt[i * WS_EPI_LD + lane];
+                if (C0) res = fmaf(p.beta.x, c0v[i], res);
+                q[(int64_t)i * 2 * p.ldc] = res;
+              }
+          }
+        } else {
+          if (C0) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const int R = Rw + i;
+              const int gi = R < p.M ? R : R - p.M, comp = R < p.M ? 0 : 1;
+              c0v[i] = (R < 2 * p.M && gj < p.N) ? C0[2 * ((int64_t)gi * p.ldc0 + gj) + comp] : 0.f;
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int R = Rw + i;
+            const int gi = R < p.M ? R : R - p.M, comp = R < p.M ? 0 : 1;
+            if (R < 2 * p.M && gj < p.N) {
+              float res = p.alpha.x * wt[i * WS_EPI_LD + lane];
+              if (C0) res = fmaf(p.beta.x, c0v[i], res);
+              C[2 * ((int64_t)gi * p.ldc + gj) + comp] = res;
+            }
           }
         }
         __syncwarp();
