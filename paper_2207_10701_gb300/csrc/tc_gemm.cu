@@ -88,10 +88,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TNR >> 3) << 17) |
                            ((uint32_t)(TM >> 4) << 24);
 
+// x_hi = x rounded to TF32 (10 mantissa bits), to nearest with ties away from zero: half a
+// TF32 unit (bit 12) added to the magnitude bits, then the 13 low bits cleared (a carry into
+// the exponent is the correct rounding up to the next binade); x_lo = x - x_hi is exact.
 __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
-  uint32_t h;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-  hi = __uint_as_float(h);
+  hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
   lo = x - hi;
 }
 
@@ -129,6 +130,31 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(bar))
       : "memory");
+}
+
+// 32 consecutive columns as two x16 loads and one wait
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[16], float (&w)[16]) {
+  uint32_t r[16], q[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];"
+      : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]),
+        "=r"(q[7]), "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]),
+        "=r"(q[14]), "=r"(q[15])
+      : "r"(taddr + 16u));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    v[i] = __uint_as_float(r[i]);
+    w[i] = __uint_as_float(q[i]);
+  }
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
@@ -699,8 +725,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_cgemm_ws_kernel(TcArgs p) {
         float v[16], w[16];
         const uint32_t ta = tmem + ((uint32_t)(32 * ew) << 16) + (uint32_t)b * WS_ACC_STRIDE +
                             (uint32_t)(c * WS_EPI_CH);
-        tmem_ld16(ta, v);
-        tmem_ld16(ta + 16, w);
+        tmem_ld32(ta, v, w);
         if (c == TNS / WS_EPI_CH - 1) {
           // the accumulator has been read: the next tile's MMAs may overwrite it
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
