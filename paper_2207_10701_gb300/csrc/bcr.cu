@@ -722,7 +722,7 @@ __device__ __forceinline__ void group_bar(int id) {
 // on every unused row (or holds no number there).
 __device__ __forceinline__ bool gjla_pivot(const float2 (&x)[GJLA_R], unsigned used, int k,
                                            int c0, int n, int lane, float2* colk, int* s_p,
-                                           float2* s_pinv, int* piv, int* rowpanel) {
+                                           float2* s_pinv, int* piv, volatile int* rowpanel) {
   constexpr int R = GJLA_R;
   float best = -1.f;
   int bi = 0x7fffffff, first = 0x7fffffff;
@@ -761,7 +761,8 @@ __device__ __forceinline__ bool gjla_pivot(const float2 (&x)[GJLA_R], unsigned u
 // in x (rows lane + 32 r); the columns are written back to the matrix at the end.
 __device__ __forceinline__ void gjla_panel(float2 (&x)[GJLA_R], int c0, int nb, int n, int ld,
                                            float2* a, float2* cbuf0, float2* cbuf1, int* s_p,
-                                           float2* s_pinv, int* piv, int* rowpanel, int* s_sing) {
+                                           float2* s_pinv, int* piv, volatile int* rowpanel,
+                                           int* s_sing) {
   constexpr int R = GJLA_R;
   const int lane = threadIdx.x & 31, t = threadIdx.x >> 5;
   unsigned used = 0;
@@ -824,8 +825,8 @@ gj_lookahead_kernel(const float2* __restrict__ src, int64_t src_stride, float2* 
   // panel start at which the row became a pivot, -1 before: the trailing group reads it for
   // the rows of panel P while the panel group sets it for rows of panel P+1 (from -1 to
   // c0 + nb); either value differs from c0 of panel P, so the reading does not depend on
-  // the order
-  int* const rowpanel = reinterpret_cast<int*>(sm_raw + L.rowpanel);
+  // the order.  All accesses are volatile (relaxed), which makes the overlap well defined.
+  volatile int* const rowpanel = reinterpret_cast<volatile int*>(sm_raw + L.rowpanel);
   int* const pinv = reinterpret_cast<int*>(sm_raw + L.pinv);
   float2* const a = reinterpret_cast<float2*>(sm_raw + L.mat);
   __shared__ int s_p[2];
