@@ -143,9 +143,9 @@ def _replica_value(ws: int, steps: int, slowest_ms: float) -> float:
 
 # DRAM bytes (read + write) per ny x ny block inverted by the FP32 look-ahead Gauss-Jordan
 # kernel, from one ncu capture of its 1010-block launch in the 200-wavelength factorisation
-# (207.5 MB read + 155.9 MB written; the kernel reads each block once and writes its inverse
+# (207.0 MB read + 154.2 MB written; the kernel reads each block once and writes its inverse
 # once, 409.6 KB algorithmic).  Only valid for ny = 160 and that kernel as it stands.
-GJ_FP32_DRAM_BYTES_PER_BLOCK_NY160 = (207.476e6 + 155.940e6) / 1010
+GJ_FP32_DRAM_BYTES_PER_BLOCK_NY160 = (206.989e6 + 154.217e6) / 1010
 # nominal dense TF32 / BF16 tensor rate (1.1 / 2.25 PFLOP/s)
 TF32_OVER_BF16 = 1.1 / 2.25
 
