@@ -994,6 +994,10 @@ cudaError_t launch_gj_cfg(cplx<T>* src, int64_t src_stride, cplx<T>* out, int64_
   return cudaGetLastError();
 }
 
+// Batched inverses of n x n blocks: FP32 blocks of n <= 160 with the look-ahead kernel
+// (block in shared memory, 1024 threads); other FP32 blocks up to 256 and FP64 blocks up to
+// 256 with the register-panel kernel (shared memory while the block fits, else in place in
+// global memory); larger blocks with gj_inverse_kernel.
 template <typename T>
 cudaError_t launch_gj(cplx<T>* src, int64_t src_stride, cplx<T>* out, int64_t out_stride, int n,
                       int batch, int32_t* status, cudaStream_t s) {
