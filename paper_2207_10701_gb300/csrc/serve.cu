@@ -208,7 +208,7 @@ void finish(rci_server* s, Request* r, const rci_result& res) {
   s->cv_work.notify_all();
 }
 
-void run_request(rci_server* s, Request* r, rci_grid* g, bool hit, rci_result* res) {
+void run_request(Request* r, rci_grid* g, bool hit, rci_result* res) {
   rci_info info{};
   rci_status st = RCI_OK;
   if (!hit) {
@@ -303,7 +303,7 @@ void worker(rci_server* s, int slot) {
     rci_grid_rebind_stream(g, stream);
     res.t_start_us = s->now_us();
     res.cache_hit = hit ? 1 : 0;
-    run_request(s, r, g, hit, &res);
+    run_request(r, g, hit, &res);
     res.t_end_us = s->now_us();
     lk.lock();
     // ---- retire: keep the factorisation resident for a keyed request, or release it
