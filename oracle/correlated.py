@@ -17,8 +17,6 @@ its own w_o and F_o = v_o^dag W v_o with v_o = A^{-dag} w_o; the trace objective
 """
 from __future__ import annotations
 
-import math
-
 import numpy as np
 
 from oracle.grid import Grid, objective_vector, planewave_source

@@ -19,7 +19,7 @@ import time
 
 import numpy as np
 
-from workloads import Workload, LIGHT_USER_LAGS
+from workloads import Workload
 from oracle.grid import Grid, rasterize_eps, objective_vector, planewave_source
 from oracle.light import W_lags, quadrature_rule
 from oracle.solve import Solver

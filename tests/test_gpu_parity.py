@@ -11,7 +11,7 @@ import pytest
 
 import workloads as W
 from oracle.grid import Grid as OGrid, rasterize_eps, stencil_coefficients, apply_A
-from oracle.light import W_lags, gauss_legendre as o_gl, quadrature_rule
+from oracle.light import W_lags, gauss_legendre as o_gl
 from oracle.reciprocal import Evaluation, qform_direct
 from oracle.solve import Solver
 

@@ -14,8 +14,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from oracle.grid import Grid, rasterize_eps, objective_vector, planewave_source, \
-    virtual_focus_kernel
+from oracle.grid import Grid, rasterize_eps, planewave_source, virtual_focus_kernel
 from oracle.light import W_lags, quadrature_rule
 from oracle.reciprocal import Evaluation, qform_direct, qform_fft, qform_spectral
 from oracle.solve import Solver

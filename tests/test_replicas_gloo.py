@@ -2,7 +2,6 @@
 and the ranks exchange nothing but the timing.  This checks that host logic with two gloo
 ranks on the CPU: disjoint design seeds, the barrier, the max over ranks and the whole-job
 value every rank derives from it."""
-import os
 import socket
 
 import pytest
