@@ -150,8 +150,13 @@ GJ_FP32_DRAM_BYTES_PER_BLOCK_NY160 = (206.989e6 + 154.217e6) / 1010
 TF32_OVER_BF16 = 1.1 / 2.25
 
 
-def _roofline(fam: str, stats: dict, prec: int, peaks: dict, peak_kind: str, ny: int = 0):
-    """Roofline record for one kernel family from the library's profiler totals."""
+def _roofline(fam: str, stats: dict, prec: int, peaks: dict, peak_kind: str, ny: int = 0,
+              live: dict | None = None):
+    """Roofline record for one kernel family from the library's profiler totals.
+
+    live: the arithmetic peaks measured in this run (rci_measure_peaks: FP32 FFMA, FP64
+    DFMA, tcgen05 TF32, ...); without them the FP32 rate is derived from unit counts and
+    clock, FP64 is nominal and TF32 a nominal ratio of the bf16 peak file."""
     ms = stats["ms"]
     if ms <= 0:
         return None
@@ -159,16 +164,25 @@ def _roofline(fam: str, stats: dict, prec: int, peaks: dict, peak_kind: str, ny:
         # 3xTF32 complex GEMMs on tcgen05: three tensor products per complex product, each
         # the 4 real products of the complex multiply -> 3x the algorithmic complex flops
         tflops = 3.0 * stats["flops"] / (ms * 1e-3) / 1e12
-        bf16 = peaks.get("bf16_tflops_sustained", 1700.0)
-        peak = bf16 * TF32_OVER_BF16
+        if live and live.get("tf32_tcgen05_tflops"):
+            peak = live["tf32_tcgen05_tflops"]
+            src = "measured in this run: tcgen05.mma kind::tf32 128x256 loop on every SM"
+        else:
+            peak = peaks.get("bf16_tflops_sustained", 1700.0) * TF32_OVER_BF16
+            src = f"{peak_kind} sustained bf16 x 1.1/2.25 (TF32)"
         return {"bound": "tensor", "achieved": round(tflops, 3), "peak": round(peak, 1),
                 "unit": "TFLOP/s", "frac": round(tflops / peak, 4), "traffic": None,
-                "kernel": fam, "peak_source": f"{peak_kind} sustained bf16 x 1.1/2.25 (TF32); "
-                "achieved counts the 3 TF32 products per complex product"}
-    if fam in ("gemm", "invert", "level0"):
+                "kernel": fam, "peak_source": src + "; achieved counts the 3 TF32 products "
+                "per complex product"}
+    if fam in ("gemm", "invert", "level0", "qform"):
         tflops = stats["flops"] / (ms * 1e-3) / 1e12
-        if prec == 0:
-            peak, src = FP64_NOMINAL_TFLOPS, "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"
+        if prec == 0 or fam == "qform":
+            if live and live.get("fp64_fma_tflops"):
+                peak, src = live["fp64_fma_tflops"], "measured in this run: FP64 DFMA loop"
+            else:
+                peak, src = FP64_NOMINAL_TFLOPS, "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"
+        elif live and live.get("fp32_fma_tflops"):
+            peak, src = live["fp32_fma_tflops"], "measured in this run: FP32 FFMA loop"
         else:
             peak = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
             src = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"
@@ -177,14 +191,9 @@ def _roofline(fam: str, stats: dict, prec: int, peaks: dict, peak_kind: str, ny:
             blocks = stats["flops"] / (8.0 * ny ** 3)      # 8 ny^3 flops per block inverse
             steps = max(1, stats.get("steps", 1))
             traffic = round(GJ_FP32_DRAM_BYTES_PER_BLOCK_NY160 * blocks / steps)
-        return {"bound": "alu", "achieved": round(tflops, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(tflops / peak, 4), "traffic": traffic,
-                "kernel": fam, "peak_source": src}
-    if fam == "qform":
-        tflops = stats["flops"] / (ms * 1e-3) / 1e12
-        return {"bound": "alu", "achieved": round(tflops, 4), "peak": FP64_NOMINAL_TFLOPS,
-                "unit": "TFLOP/s", "frac": round(tflops / FP64_NOMINAL_TFLOPS, 4),
-                "traffic": None, "kernel": fam, "peak_source": "FP64 nominal"}
+        return {"bound": "alu", "achieved": round(tflops, 4 if fam == "qform" else 3),
+                "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(tflops / peak, 4),
+                "traffic": traffic, "kernel": fam, "peak_source": src}
     gbs = stats["bytes"] / (ms * 1e-3) / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
     return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
@@ -192,15 +201,16 @@ def _roofline(fam: str, stats: dict, prec: int, peaks: dict, peak_kind: str, ny:
             "peak_source": f"{peak_kind} HBM copy bandwidth"}
 
 
-def _cpu_baseline(timeout_s: float = 240.0):
-    """The oracle as it stands, one cold C2 evaluation, single-threaded, in a child."""
+def _cpu_baseline(seed: int, timeout_s: float = 240.0):
+    """The oracle as it stands, one cold C2 evaluation of design `seed`, single-threaded, in
+    a child process; also returns the oracle's F of that design."""
     code = (
         "import sys,time,json; sys.path.insert(0, %r)\n"
         "import workloads as W\n"
         "from oracle.reciprocal import timed_reciprocal\n"
-        "wl = W.c2_collimator(); ws = W.widths(500, 12345)\n"
+        "wl = W.c2_collimator(); ws = W.widths(500, %d)\n"
         "F, t = timed_reciprocal(wl, ws)\n"
-        "print(json.dumps({'F': F, 'seconds': t}))\n" % ROOT)
+        "print(json.dumps({'F': F, 'seconds': t}))\n" % (ROOT, seed))
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
               "NUMEXPR_NUM_THREADS", "VECLIB_MAXIMUM_THREADS"):
@@ -212,12 +222,29 @@ def _cpu_baseline(timeout_s: float = 240.0):
         d = json.loads(r.stdout.strip().splitlines()[-1])
     except Exception as e:  # noqa: BLE001
         return {"value": None, "unit": "evals/s", "cores": 1, "kind": "oracle",
-                "sample": f"failed: {type(e).__name__}"}
+                "sample": f"failed: {type(e).__name__}"}, None
     return {"value": round(1.0 / d["seconds"], 5), "unit": "evals/s", "cores": 1,
             "kind": "oracle", "seconds_per_eval": round(d["seconds"], 3),
             "sample": "one cold evaluation of the full 200-lambda workload (raster, assembly, "
                       "SuperLU factor, double-double refined solve, direct quadratic form), "
-                      "single thread"}
+                      "single thread, on the design of the first timed GPU evaluation"}, d["F"]
+
+
+def _golden(name: str, seed: int):
+    """The oracle's stored values for a full-size design (written by tests/golden/
+    make_golden.py, which runs only the oracle), or None."""
+    p = os.path.join(ROOT, "tests", "golden", f"{name}_seed{seed}.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        return json.load(f)
+
+
+def _config(nx, ny, unknowns, prec_name, S, ws_):
+    return {"workload": WORKLOAD, "nx": nx, "ny": ny, "unknowns": unknowns, "cells": 500,
+            "light": "annulus 10-30 deg", "objective": "planewave mode, 0 deg",
+            "precision": prec_name, "parallelism": f"replicas x{ws_}",
+            "concurrent_evaluations": S}
 
 
 def run_reference(args):
@@ -249,8 +276,8 @@ def run_reference(args):
         "ms_per_step": round(total / k_run * 1e3, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "p50_ms": round(statistics.median(ms), 2), "p99_ms": round(max(ms), 2),
-        "config": {"workload": WORKLOAD, "nx": 4040, "ny": 160, "unknowns": 646400,
-                   "light": "annulus 10-30 deg", "objective": "planewave mode, 0 deg"},
+        "config": dict(_config(4040, 160, 646400, "fp64", 1, 1),
+                       l2="no flush: the oracle's LU factors exceed the host caches"),
         "cpu_baseline": {"value": round(value, 5), "unit": "evals/s", "cores": 1,
                          "kind": "oracle",
                          "sample": f"{k_run} of {args.steps} cold evaluations of the full workload "
@@ -277,6 +304,8 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     peaks, peak_kind = _peaks()
+    # arithmetic peaks of this GPU, measured now (the rooflines divide by them)
+    live = P.measure_peaks(local) if rank == 0 else None
     wl = W.WORKLOADS[WORKLOAD]()
     prec = P.FP64 if args.prec == "fp64" else P.FP32_REFINE
     nc = wl.grid.n_cells
@@ -382,10 +411,11 @@ def run_ours(args):
     if rank == 0:
         fams = {f: v for f, v in prof.items() if v["ms"] > 0}
         dom = max(fams, key=lambda f: fams[f]["ms"])
-        roof = _roofline(dom, dict(fams[dom], steps=K1), prec, peaks, peak_kind, ny=wl.grid.ny)
+        roof = _roofline(dom, dict(fams[dom], steps=K1), prec, peaks, peak_kind, ny=wl.grid.ny,
+                         live=live)
         kernels = {}
         for f, v in fams.items():
-            r = _roofline(f, dict(v, steps=K1), prec, peaks, peak_kind, ny=wl.grid.ny)
+            r = _roofline(f, dict(v, steps=K1), prec, peaks, peak_kind, ny=wl.grid.ny, live=live)
             kernels[f] = {"ms_per_step": round(v["ms"] / K1, 4),
                           "share": round(v["ms"] / sum(x["ms"] for x in fams.values()), 4),
                           "launches_per_step": v["launches"] / K1,
@@ -403,21 +433,21 @@ def run_ours(args):
             "p99_ms": round(ps[min(len(ps) - 1, int(math.ceil(0.99 * len(ps))) - 1)], 4),
             "latency_alone": {"p50_ms": round(lat1[len(lat1) // 2], 4),
                               "p99_ms": round(lat1[-1], 4), "evals": len(lat1)},
-            "config": {"workload": WORKLOAD, "nx": g.nx, "ny": g.ny, "unknowns": g.N,
-                       "cells": nc, "light": "annulus 10-30 deg",
-                       "objective": "planewave mode, 0 deg",
-                       "precision": args.prec, "parallelism": f"replicas x{ws_}",
-                       "concurrent_evaluations": S,
-                       "l2": "no flush: factor store %.2f GB > 129 MB L2"
-                             % (g.device_bytes() / 1e9),
-                       "refine_iters_mean": round(sum(i.refine_iters for i in infos) / K, 2),
-                       "rel_residual_max": max(i.rel_residual for i in infos)},
+            "config": dict(_config(g.nx, g.ny, g.N, args.prec, S, ws_),
+                           l2="no flush: factor store %.2f GB > 129 MB L2"
+                              % (g.device_bytes() / 1e9),
+                           refine_iters_mean=round(sum(i.refine_iters for i in infos) / K, 2),
+                           rel_residual_max=max(i.rel_residual for i in infos),
+                           fp64_fallbacks=sum(1 for i in infos if i.fallback)),
+            "measured_peaks": {k: (round(v, 3) if isinstance(v, float) else v)
+                               for k, v in (live or {}).items()},
             "gpu_launches": int(launches),
             "roofline": roof,
             "kernels": kernels,
             "clocks": clk,
             "e2e": {"value": round(e2e_value, 3), "unit": "evals/s",
                     "h2d_bytes_per_step": 8 * nc, "d2h_bytes_per_step": int(round(d2h))},
+            "F_first": Fs[0],
             "F_last": Fs[-1],
         }
     for gw in grids:
@@ -525,10 +555,25 @@ def run_ours(args):
                             "device_gb": round(g5.device_bytes() / 1e9, 2)}
         c3["rel_diff_fp32_refine_vs_fp64"] = (abs(c3["fp32_refine"]["F"] - c3["fp64"]["F"])
                                               / abs(c3["fp64"]["F"]))
+        gold = _golden(w3.name, 0)
+        if gold is not None:
+            c3["F_oracle"] = gold["F"]
+            for name in ("fp32_refine", "fp64"):
+                c3[name]["rel_err_vs_oracle"] = abs(c3[name]["F"] - gold["F"]) / abs(gold["F"])
         extra["c3_precision"] = c3
         line.update(extra)
+    if rank == 0 and not args.quick and not args.no_serve_leg:
+        line["serving"] = _serving_leg(args, local)
     if rank == 0 and not args.no_cpu_baseline and ws_ == 1:
-        line["cpu_baseline"] = _cpu_baseline()
+        # the oracle on the design of the first timed evaluation: its time is the CPU
+        # baseline, its F the per-result error of that evaluation
+        cb, F_or = _cpu_baseline(Wm)
+        line["cpu_baseline"] = cb
+        if F_or is not None:
+            line["rel_err_vs_oracle"] = {"F_gpu": Fs[0], "F_oracle": F_or,
+                                         "rel_err": abs(Fs[0] - F_or) / abs(F_or),
+                                         "tolerance": 1e-8 if prec == P.FP32_REFINE else 1e-9,
+                                         "design_seed": Wm}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws_ > 1:
@@ -537,26 +582,17 @@ def run_ours(args):
     return 0
 
 
-def run_serve(args):
-    """Serving form: a stream of requests with Poisson arrivals (metasurfaces of 50..1250
-    cells, concentrator / collimator, cone / annulus, 30 % with the gradient) admitted
-    continuously by the library's server; p50/p99 latency from submission to result and
-    completed evaluations per second.  The arrival rate defaults to 70 % of the capacity
-    measured on a closed-loop burst of the same distribution."""
+def _serve_stream(P, W, local, n_requests, burst, slots, arena_gb, cache_gb, repeat, rate=0.0):
+    """Requests with Poisson arrivals (metasurfaces of 50..1250 cells, concentrator /
+    collimator, cone / annulus, 30 % with the gradient; `repeat` of them re-evaluating one
+    of the last 32 designs under new light) admitted continuously by the library's server.
+    The arrival rate defaults to 70 % of the capacity measured on a closed-loop burst."""
     import numpy as np
-    import torch
 
-    import workloads as W
-    import paper_2207_10701_gb300 as P
-    from paper_2207_10701_gb300 import build as B
-
-    ws_, rank, local = _dist()
-    if rank != 0:
-        return 0
-    B.build()
-    torch.cuda.set_device(local)
-    slots, arena = args.serve_slots, int(args.serve_arena_gb * (1 << 30))
-    with P.Server(device=local, slots=slots, arena_bytes=arena, lookahead=8) as srv:
+    arena = int(arena_gb * (1 << 30))
+    cache = int(cache_gb * (1 << 30))
+    with P.Server(device=local, slots=slots, arena_bytes=arena, cache_bytes=cache,
+                  lookahead=8) as srv:
         def run(reqs, paced):
             t_start = time.perf_counter()
             tickets = [None] * len(reqs)
@@ -568,7 +604,7 @@ def run_serve(args):
                         if dt > 0:
                             time.sleep(dt)
                     tickets[k] = srv.submit(r.grid, r.widths, r.objective, r.light,
-                                            want_grad=r.want_grad)
+                                            want_grad=r.want_grad, design_key=r.design_key)
             th = threading.Thread(target=submitter)
             th.start()
             out = []
@@ -581,11 +617,13 @@ def run_serve(args):
 
         # warm-up (kernels loaded, arena touched) and closed-loop capacity
         run(W.serving_requests(16, 0.0, seed=999), paced=False)
-        burst = run(W.serving_requests(args.serve_burst, 0.0, seed=998), paced=False)
-        span = (max(r["t_end_us"] for r in burst) - min(r["t_submit_us"] for r in burst)) * 1e-6
-        capacity = len(burst) / span
-        rate = args.serve_rate if args.serve_rate > 0 else 0.7 * capacity
-        reqs = W.serving_requests(args.serve_requests, rate, seed=1)
+        bq = W.serving_requests(burst, 0.0, seed=998, repeat_fraction=repeat)
+        burst_res = run(bq, paced=False)
+        span = (max(r["t_end_us"] for r in burst_res)
+                - min(r["t_submit_us"] for r in burst_res)) * 1e-6
+        capacity = len(burst_res) / span
+        rate = rate if rate > 0 else 0.7 * capacity
+        reqs = W.serving_requests(n_requests, rate, seed=1, repeat_fraction=repeat)
         st0 = srv.stats()
         clocks = ClockSampler(local)
         clocks.start()
@@ -594,28 +632,59 @@ def run_serve(args):
         st = srv.stats()
     lat = np.array([(r["t_end_us"] - r["t_submit_us"]) * 1e-3 for r in res])
     wait = np.array([(r["t_start_us"] - r["t_submit_us"]) * 1e-3 for r in res])
-    ok = [r["status"] in (0, 6) for r in res]
+    ok = [r["status"] == 0 for r in res]             # converged to the tolerance
+    unconverged = sum(1 for r in res if r["status"] == 6)   # RCI_ENOCONV: value not counted
     span = (max(r["t_end_us"] for r in res) - min(r["t_submit_us"] for r in res)) * 1e-6
     grad = np.array([q.want_grad for q in reqs])
-    line = {
-        "metric": "serving: reciprocal evaluations/s under Poisson arrivals, p50/p99 latency",
-        "value": round(sum(ok) / span, 3), "unit": "evals/s", "n_gpus": 1,
-        "higher_is_better": True, "impl": "ours", "dtype": "f32+f64refine", "data": "synthetic",
+    delta = ("submitted", "completed", "failed", "admission_waits", "bypasses", "cache_hits",
+             "cache_evictions")
+    return {
+        "value": round(sum(ok) / span, 3), "unit": "evals/s",
         "p50_ms": round(float(np.percentile(lat, 50)), 3),
         "p99_ms": round(float(np.percentile(lat, 99)), 3),
         "p50_queue_ms": round(float(np.percentile(wait, 50)), 3),
         "p99_queue_ms": round(float(np.percentile(wait, 99)), 3),
         "p50_ms_gradient": round(float(np.percentile(lat[grad], 50)), 3) if grad.any() else None,
-        "requests": len(reqs), "failed": len(reqs) - sum(ok),
+        "requests": len(reqs), "failed": len(reqs) - sum(ok), "unconverged": unconverged,
+        "repeated_designs": round(repeat, 3),
         "arrival_rate_per_s": round(rate, 3), "capacity_evals_per_s": round(capacity, 3),
         "config": {"workload": "serving stream: 50-1250 cells log-uniform, ny 160, "
                                "concentrator/collimator, cone/annulus, 30% gradient",
-                   "slots": slots, "arena_gb": args.serve_arena_gb, "lookahead": 8},
-        "server": {k: st[k] - st0.get(k, 0) if k in ("submitted", "completed", "failed",
-                                                     "admission_waits", "bypasses") else st[k]
-                   for k in st},
+                   "slots": slots, "arena_gb": arena_gb, "cache_gb": cache_gb, "lookahead": 8},
+        "server": {k: st[k] - st0.get(k, 0) if k in delta else st[k] for k in st},
         "clocks": clk,
     }
+
+
+def _serving_leg(args, local):
+    """The serving form inside the default line: a compact stream (512 requests by default)
+    with repeated designs, a factorisation cache and an arena small enough that admission
+    has to wait for memory."""
+    import workloads as W
+    import paper_2207_10701_gb300 as P
+    return _serve_stream(P, W, local, args.serve_leg_requests, 48, 6, 24.0, 6.0, 0.25)
+
+
+def run_serve(args):
+    """Serving form as its own line (--serve): the full 4096-request stream."""
+    import torch
+
+    import workloads as W
+    import paper_2207_10701_gb300 as P
+    from paper_2207_10701_gb300 import build as B
+
+    ws_, rank, local = _dist()
+    if rank != 0:
+        return 0
+    B.build()
+    torch.cuda.set_device(local)
+    d = _serve_stream(P, W, local, args.serve_requests, args.serve_burst, args.serve_slots,
+                      args.serve_arena_gb, args.serve_cache_gb, args.serve_repeat,
+                      rate=args.serve_rate)
+    line = {"metric": "serving: reciprocal evaluations/s under Poisson arrivals, p50/p99 latency",
+            "n_gpus": 1, "higher_is_better": True, "impl": "ours", "dtype": "f32+f64refine",
+            "data": "synthetic"}
+    line.update(d)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -639,6 +708,12 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=6)
     ap.add_argument("--serve-burst", type=int, default=96)
     ap.add_argument("--serve-arena-gb", type=float, default=96.0)
+    ap.add_argument("--serve-cache-gb", type=float, default=0.0)
+    ap.add_argument("--serve-repeat", type=float, default=0.0,
+                    help="fraction of requests re-evaluating a recent design")
+    ap.add_argument("--serve-leg-requests", type=int, default=512,
+                    help="requests of the serving leg in the default line")
+    ap.add_argument("--no-serve-leg", action="store_true")
     args = ap.parse_args()
     if args.serve:
         return run_serve(args)

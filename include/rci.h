@@ -388,6 +388,36 @@ rci_status rci_profile_read(rci_grid* g, rci_profile* out);
 /* Kernels launched by this library in this process so far. */
 uint64_t rci_kernel_launches(void);
 
+/* Failure detection: every wait of a tensor-core pipeline stage (operand buffers,
+ * accumulators) spins at most `cycles` SM clock cycles; a wait that runs out ends its
+ * kernel (no trap), which records a device status that the next rci_factor / rci_solve
+ * returns as RCI_ETIMEOUT; the kernel still waits, at the default limit, for its own
+ * tensor-core operations before it frees its tensor memory, so the context stays usable.
+ * Process-wide, applies to launches that start after the call; cycles <= 0 restores the
+ * default (4e9 cycles, about 2 s).  Returns the previous limit.  Meant for tests of the
+ * timeout path: a limit of a few hundred cycles makes the first pipeline wait run out. */
+int64_t rci_set_wait_limit(int64_t cycles);
+
+/* Arithmetic peaks of a device, measured by small loops on every SM, each about 30 ms
+ * timed with CUDA events (instrumentation; the roofline fractions of the solver's kernels
+ * divide by these).  FP32 FFMA and FP64 DFMA chains; the legacy warp-level FP64 (DMMA,
+ * mma.sync m8n8k4) and INT8 (IMMA, mma.sync m16n8k32 s8) tensor paths -- sm_103a's
+ * tcgen05 tensor cores take no INT8 operands; tcgen05.mma 128 x 256 from shared memory
+ * in TF32 and in BF16.  Rates in 1e12 operations per second (a multiply-add counts 2).
+ * Runs on its own stream and synchronises it; allocates a few bytes of device memory.
+ * Errors: ECUDA, ETIMEOUT (a tensor-core probe's bounded completion wait expired). */
+typedef struct {
+  double fp32_fma_tflops;
+  double fp64_fma_tflops;
+  double fp64_dmma_tflops;
+  double int8_imma_tops;
+  double tf32_tcgen05_tflops;
+  double bf16_tcgen05_tflops;
+  int32_t sm_count;
+  int32_t reserved;
+} rci_peaks;
+rci_status rci_measure_peaks(int device, rci_peaks* out);
+
 /* Static strings; never NULL. */
 const char* rci_status_str(rci_status s);
 const char* rci_last_error(const rci_grid* g);

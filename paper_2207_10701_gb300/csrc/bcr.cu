@@ -2010,6 +2010,13 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
   }
   sbytes += (double)nn * sizeof(cplx<T>) + 2.0 * nx * (double)ny * nrhs * sizeof(cplx<T>);
   ProfScope ps(h->prof, PF_SOLVE, s, sflops, sbytes, 0);
+  // kernels this solve launches (level-0 pair, per dense level forward and backward, the
+  // single remaining row); several right-hand sides run the level products as GEMMs
+  {
+    const int dense = h->Lf - 1, l0 = m0 > 0 ? 1 : 0;
+    ps.nl = nrhs == 1 ? l0 + 1 + 2 * dense + 1 + dense + 1
+                      : l0 + 1 + 4 * dense + 1 + 3 * dense + 1 + l0;
+  }
 
   if (nrhs == 1) {
     if (ny % vec16<T>::per != 0 || ny > 256 * vec16<T>::per)

@@ -12,6 +12,7 @@
 
 #include "bcr.cuh"
 #include "kernels.cuh"
+#include "tc_gemm.cuh"
 
 static std::atomic<uint64_t> g_launches{0};
 void rci_note_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
@@ -512,10 +513,13 @@ const char* rci_status_str(rci_status s) {
 
 const char* rci_last_error(const rci_grid* g) { return g ? g->err.c_str() : ""; }
 
-rci_status rci_destroy_grid(rci_grid* g) {
-  if (!g) return RCI_OK;
+}  // extern "C"
+
+namespace {
+// Release a grid's memory and events; with sync, after draining the grid's stream.
+void destroy_grid(rci_grid* g, bool sync) {
   DeviceGuard dg(g->device);
-  if (g->s) cudaStreamSynchronize(g->s);
+  if (sync && g->s) cudaStreamSynchronize(g->s);
   void* ps[] = {g->widths, g->eps, g->dg, g->cx, g->cy, g->dg0, g->kss, g->b1, g->x1, g->r1, g->r32, g->d32,
                 g->crow, g->vsrc, g->lags, g->qpart, g->dscal, g->part_r, g->part_b, g->ratio,
                 g->vf_scratch, g->dstatus, g->mb, g->mx, g->mr, g->m32a, g->m32b, g->th_d,
@@ -531,6 +535,20 @@ rci_status rci_destroy_grid(rci_grid* g) {
   for (cudaEvent_t e : g->ev)
     if (e) cudaEventDestroy(e);
   delete g;
+}
+}  // namespace
+
+// A grid with no device work pending (its stream drained by the caller after its last
+// call): released without waiting on the stream, which may since carry other work.
+void rci_grid_destroy_idle(rci_grid* g) {
+  if (g) destroy_grid(g, false);
+}
+
+extern "C" {
+
+rci_status rci_destroy_grid(rci_grid* g) {
+  if (!g) return RCI_OK;
+  destroy_grid(g, true);
   return RCI_OK;
 }
 
@@ -1144,6 +1162,12 @@ rci_status rci_set_refinement(rci_grid* g, double tol, int32_t max_steps) {
 }
 
 uint64_t rci_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int64_t rci_set_wait_limit(int64_t cycles) {
+  const long long old = tc_wait_limit();
+  tc_set_wait_limit((long long)cycles);
+  return (int64_t)old;
+}
 
 rci_status rci_profile_enable(rci_grid* g, int on) {
   if (!g) return RCI_EINVAL;

@@ -116,24 +116,24 @@ static_assert(RCI_QFORM_NOALLOC_MAX_N % QT == 0, "maximum size must be a whole n
 static __device__ __align__(256) double g_qform_noalloc_scratch[NOALLOC_PARTIALS];
 
 namespace {
-std::once_flag g_noalloc_once[NOALLOC_MAX_DEVICES];
-cudaError_t g_noalloc_err[NOALLOC_MAX_DEVICES];
+std::mutex g_noalloc_mu;
 double* g_noalloc_ptr[NOALLOC_MAX_DEVICES];
 
 // Device address of the scratch array on the current device.  In host code the array's
-// name is only a host-side stand-in, so the address is looked up once per device (with
-// that device current) and cached.
+// name is only a host-side stand-in, so the address is looked up with that device current
+// and cached once found; a failed lookup is not cached, so a later call tries again.
 cudaError_t noalloc_scratch(double** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
-  std::call_once(g_noalloc_once[dev], [dev]() {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
     void* p = nullptr;
-    g_noalloc_err[dev] = cudaGetSymbolAddress(&p, g_qform_noalloc_scratch);
+    e = cudaGetSymbolAddress(&p, g_qform_noalloc_scratch);
+    if (e != cudaSuccess) return e;
     g_noalloc_ptr[dev] = static_cast<double*>(p);
-  });
-  if (g_noalloc_err[dev] != cudaSuccess) return g_noalloc_err[dev];
+  }
   *out = g_noalloc_ptr[dev];
   return cudaSuccess;
 }

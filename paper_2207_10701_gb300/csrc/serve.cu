@@ -32,6 +32,7 @@ rci_status rci_grid_alloc_with(const rci_grid_desc* desc, cudaStream_t stream, c
                                int with_grad, rci_grid** out);
 rci_status rci_grid_init(rci_grid* g);
 void rci_grid_rebind_stream(rci_grid* g, cudaStream_t s);
+void rci_grid_destroy_idle(rci_grid* g);
 
 namespace {
 
@@ -121,12 +122,14 @@ size_t arena_largest_free(rci_server* s) {
 }
 
 // Drop the least recently used resident grid nobody is using (caller holds s->mu).
-// The grid's stream is drained by rci_destroy_grid before its memory returns to the arena.
+// A resident grid has no device work pending (its worker drained the slot's stream before
+// retiring it), so its memory returns to the arena at once, without waiting on the stream
+// it last ran on, which another slot's request may be using by now.
 bool evict_one(rci_server* s) {
   for (auto it = s->cache.end(); it != s->cache.begin();) {
     --it;
     if (it->pinned) continue;
-    rci_destroy_grid(it->g);
+    rci_grid_destroy_idle(it->g);
     s->cache_bytes -= it->bytes;
     s->cache.erase(it);
     s->st.cache_evictions++;
@@ -304,6 +307,9 @@ void worker(rci_server* s, int slot) {
     res.t_start_us = s->now_us();
     res.cache_hit = hit ? 1 : 0;
     run_request(r, g, hit, &res);
+    // nothing of this request stays queued on the slot's stream once it is retired (an
+    // evaluation that failed part-way may have left work behind)
+    cudaStreamSynchronize(stream);
     res.t_end_us = s->now_us();
     lk.lock();
     // ---- retire: keep the factorisation resident for a keyed request, or release it

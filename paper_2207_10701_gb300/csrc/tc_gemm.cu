@@ -25,6 +25,8 @@
 // 32 (w % 4).., columns half (w / 4)).
 // Every wait is bounded: on timeout the kernel records DEV_TIMEOUT in *status, skips
 // the epilogue, frees its tensor memory and returns.
+#include <atomic>
+
 #include "common.cuh"
 #include "tc_gemm.cuh"
 
@@ -63,6 +65,7 @@ struct TcArgs {
   float2 alpha, beta;
   int32_t* status;
   int batch;
+  long long wait_limit;  // SM clock cycles a pipeline wait may take before the kernel gives up
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -100,8 +103,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-// true when the phase with the given parity has completed; false after the time limit
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// true when the phase with the given parity has completed; false after `limit` cycles
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          long long limit = WAIT_LIMIT_CYCLES) {
   const uint32_t a = smem_u32(bar);
   const long long t0 = clock64();
   while (true) {
@@ -113,7 +117,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > WAIT_LIMIT_CYCLES) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 
@@ -272,7 +276,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) tc_cgemm_kernel(TcArgs p) {
       if (kb + PF < nkb) load_stage(kb + PF, av[(g + PF) % RING], bv[(g + PF) % RING]);
       if (kb >= NSTAGE) {
         // the MMAs that last read this buffer must have completed
-        if (!mbar_wait(&mbar[st], (uint32_t)((kb / NSTAGE - 1) & 1))) ok = false;
+        if (!mbar_wait(&mbar[st], (uint32_t)((kb / NSTAGE - 1) & 1), p.wait_limit)) ok = false;
       }
       if (__syncthreads_or(!ok)) {
         ok = false;
@@ -438,7 +442,8 @@ static_assert(WS_PROD_WARPS * 32 == TC_THREADS, "the staging map assumes 256 thr
 static_assert(TNS % WS_EPI_CH == 0, "whole epilogue chunks");
 
 // bounded wait that also ends when another role has given up
-__device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                        long long limit) {
   const uint32_t a = smem_u32(bar);
   const long long t0 = clock64();
   while (true) {
@@ -451,7 +456,7 @@ __device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, volatile
         : "memory");
     if (done) return true;
     if (*abort_flag) return false;
-    if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
+    if (clock64() - t0 > limit) {
       *abort_flag = 1;
       return false;
     }
@@ -619,7 +624,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_cgemm_ws_kernel(TcArgs p) {
         if (it >= WS_NSTAGE) {
           // one lane per warp polls the barrier
           bool got = true;
-          if (lane == 0) got = ws_wait(&empty[st], (uint32_t)((it / WS_NSTAGE - 1) & 1), abort_flag);
+          if (lane == 0)
+            got = ws_wait(&empty[st], (uint32_t)((it / WS_NSTAGE - 1) & 1), abort_flag, p.wait_limit);
           if (!__shfl_sync(0xffffffffu, got, 0)) {
             ok = false;
             break;
@@ -673,12 +679,14 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_cgemm_ws_kernel(TcArgs p) {
       int it = 0;
       for (int tl = 0; tl < ntl && ok; ++tl) {
         const int b = tl & 1;
-        if (tl >= 2 && !ws_wait(&accempty[b], (uint32_t)((tl / 2 - 1) & 1), abort_flag)) break;
+        if (tl >= 2 &&
+            !ws_wait(&accempty[b], (uint32_t)((tl / 2 - 1) & 1), abort_flag, p.wait_limit))
+          break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t acc = tmem + (uint32_t)b * WS_ACC_STRIDE;
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int st = it % WS_NSTAGE;
-          if (!ws_wait(&full[st], (uint32_t)((it / WS_NSTAGE) & 1), abort_flag)) {
+          if (!ws_wait(&full[st], (uint32_t)((it / WS_NSTAGE) & 1), abort_flag, p.wait_limit)) {
             ok = false;
             break;
           }
@@ -711,7 +719,11 @@ __global__ void __launch_bounds__(WS_THREADS, 1) tc_cgemm_ws_kernel(TcArgs p) {
     float* wt = epi + ew * 32 * WS_EPI_LD;
     for (int tl = 0; tl < ntl; ++tl) {
       const int b = tl & 1;
-      if (!ws_wait(&accfull[b], (uint32_t)((tl / 2) & 1), abort_flag)) break;
+      // lane 0 polls and the warp follows its verdict: tcgen05.ld below is .sync.aligned,
+      // so the whole warp must either go on to it or leave together
+      bool got = true;
+      if (lane == 0) got = ws_wait(&accfull[b], (uint32_t)((tl / 2) & 1), abort_flag, p.wait_limit);
+      if (!__shfl_sync(0xffffffffu, got, 0)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int tile = (int)blockIdx.x + tl * (int)gridDim.x;
       const int z = tile / mt;
@@ -806,13 +818,22 @@ int sm_count() {
 
 }  // namespace
 
+static std::atomic<long long> g_wait_limit{WAIT_LIMIT_CYCLES};
+
+long long tc_wait_limit() { return g_wait_limit.load(std::memory_order_relaxed); }
+
+void tc_set_wait_limit(long long cycles) {
+  g_wait_limit.store(cycles > 0 ? cycles : WAIT_LIMIT_CYCLES, std::memory_order_relaxed);
+}
+
 cudaError_t launch_tc_cgemm(int M, int N, int K, bool ta, bool tb, float2 alpha, const float2* A,
                             int64_t lda, int64_t sA, const float2* B, int64_t ldb, int64_t sB,
                             float2 beta, const float2* C0, int64_t ldc0, int64_t sC0, float2* C,
                             int64_t ldc, int64_t sC, int batch, int32_t* status, cudaStream_t s) {
   if (batch <= 0) return cudaSuccess;
   if (batch > 65535 || M < 1 || N < 1 || K < 1) return cudaErrorInvalidValue;
-  TcArgs a{M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, C0, ldc0, sC0, alpha, beta, status, batch};
+  TcArgs a{M,   N,   K,    A,   lda,   sA,   B,      ldb,   sB, C, ldc, sC, C0,
+           ldc0, sC0, alpha, beta, status, batch, tc_wait_limit()};
   dim3 grd((unsigned)ceil_div(N, TNC), (unsigned)ceil_div(M, TM), (unsigned)batch);
   auto launch = [&](auto kern) -> cudaError_t {
     RCI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -10,3 +10,9 @@ cudaError_t launch_tc_cgemm(int M, int N, int K, bool ta, bool tb, float2 alpha,
                             int64_t lda, int64_t sA, const float2* B, int64_t ldb, int64_t sB,
                             float2 beta, const float2* C0, int64_t ldc0, int64_t sC0, float2* C,
                             int64_t ldc, int64_t sC, int batch, int32_t* status, cudaStream_t s);
+
+// Cycles a pipeline wait inside the tensor-core kernels may spin before the kernel gives
+// up with DEV_TIMEOUT (process-wide; <= 0 restores the default of 4e9 cycles, ~2 s).  The
+// wait for the kernel's own MMAs before its tensor memory is freed always keeps the default.
+long long tc_wait_limit();
+void tc_set_wait_limit(long long cycles);

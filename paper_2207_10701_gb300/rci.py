@@ -80,6 +80,13 @@ class ProfileC(C.Structure):
                 ("launches", C.c_int64 * 8)]
 
 
+class PeaksC(C.Structure):
+    _fields_ = [("fp32_fma_tflops", C.c_double), ("fp64_fma_tflops", C.c_double),
+                ("fp64_dmma_tflops", C.c_double), ("int8_imma_tops", C.c_double),
+                ("tf32_tcgen05_tflops", C.c_double), ("bf16_tcgen05_tflops", C.c_double),
+                ("sm_count", C.c_int32), ("reserved", C.c_int32)]
+
+
 @dataclasses.dataclass
 class Info:
     refine_iters: int
@@ -140,6 +147,8 @@ EXPORTED = {
     "rci_profile_enable": (C.c_int, [_P, C.c_int]),
     "rci_profile_read": (C.c_int, [_P, C.POINTER(ProfileC)]),
     "rci_kernel_launches": (C.c_uint64, []),
+    "rci_set_wait_limit": (C.c_int64, [C.c_int64]),
+    "rci_measure_peaks": (C.c_int, [C.c_int, C.POINTER(PeaksC)]),
     "rci_status_str": (C.c_char_p, [C.c_int]),
     "rci_last_error": (C.c_char_p, [_P]),
 }
@@ -407,6 +416,19 @@ def kernel_launches() -> int:
     return int(lib().rci_kernel_launches())
 
 
+def measure_peaks(device: int = 0) -> dict:
+    """Measured arithmetic peaks of the device (rci_measure_peaks), rates in 1e12 ops/s."""
+    p = PeaksC()
+    _check(lib().rci_measure_peaks(device, C.byref(p)))
+    return {n: getattr(p, n) for n, _ in PeaksC._fields_ if n != "reserved"}
+
+
+def set_wait_limit(cycles: int) -> int:
+    """Cycles a tensor-core pipeline wait may spin before its kernel gives up with
+    RCI_ETIMEOUT (process-wide; <= 0 restores the default).  Returns the previous limit."""
+    return int(lib().rci_set_wait_limit(int(cycles)))
+
+
 def qform_toeplitz(v, lags, stream=None) -> float:
     """sum_{i,l} conj(v_i) lags[|i-l|] v_l on the device (v complex128, lags float64, CUDA)."""
     torch = _torch()
@@ -428,8 +450,18 @@ def qform_toeplitz_noalloc(v, lags, out, stream=None):
     torch = _torch()
     if v.dtype != torch.complex128 or lags.dtype != torch.float64 or out.dtype != torch.float64:
         raise TypeError("v complex128, lags and out float64")
+    # the library receives raw device pointers: a host tensor, or one on another device than
+    # the current one, would hand the kernel memory it cannot (or must not) address
+    dev = torch.cuda.current_device()
+    for name, t in (("v", v), ("lags", lags), ("out", out)):
+        if not t.is_cuda or t.device.index != dev:
+            raise ValueError(f"{name} must be a CUDA tensor on the current device (cuda:{dev})")
     if not (v.is_contiguous() and lags.is_contiguous()):
         raise ValueError("contiguous tensors required")
+    if lags.numel() < v.numel():
+        raise ValueError("lags needs one entry per lag |i - l| < n (lags.numel() >= v.numel())")
+    if out.numel() < 1:
+        raise ValueError("out needs one element")
     _check(lib().rci_qform_toeplitz_noalloc(_dptr(v), _dptr(lags), v.numel(), _dptr(out),
                                             _stream(stream)))
     return out

@@ -86,3 +86,17 @@ def test_peaks_fall_back_without_the_measured_file(tmp_path, monkeypatch):
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 7000.0}))
     peaks, kind = bench._peaks()
     assert kind == "measured" and peaks["hbm_gbs"] == 7000.0
+
+
+def test_measured_peaks_of_the_run_replace_the_derived_ones():
+    live = {"fp32_fma_tflops": 70.0, "fp64_fma_tflops": 1.1, "tf32_tcgen05_tflops": 1000.0}
+    st = {"ms": 10.0, "flops": 1.0e12, "bytes": 0.0, "steps": 1}
+    g = bench._roofline("gemm", st, 1, PEAKS, "measured", live=live)
+    assert g["peak"] == 1000.0 and "measured in this run" in g["peak_source"]
+    assert g["frac"] == pytest.approx(300.0 / 1000.0, rel=1e-3)
+    inv = bench._roofline("invert", st, 1, PEAKS, "measured", ny=96, live=live)
+    assert inv["peak"] == 70.0 and inv["frac"] == pytest.approx(100.0 / 70.0, rel=1e-3)
+    g64 = bench._roofline("gemm", st, 0, PEAKS, "measured", live=live)
+    assert g64["peak"] == 1.1
+    q = bench._roofline("qform", st, 1, PEAKS, "measured", live=live)
+    assert q["peak"] == 1.1 and q["bound"] == "alu"

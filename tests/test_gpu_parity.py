@@ -157,9 +157,9 @@ def test_avg_intensity_c2_full_size(prec):
     F, info = g.avg_intensity(wl.objective, wl.light)
     assert abs(F - F_ref) <= TOL_F[prec] * F_ref, (F, F_ref, info)
     v, _ = g.solve_reciprocal(wl.objective)
-    idx = np.random.default_rng(0).choice(v.numel(), 64, replace=False)
-    vs = _cplx(v)[idx]
-    assert np.max(np.abs(vs - v_ref[idx])) <= TOL_F[prec] * np.max(np.abs(v_ref))
+    v = _cplx(v)                              # the whole source-plane field, 4000 points
+    assert v.shape == v_ref.shape
+    assert np.max(np.abs(v - v_ref)) <= TOL_F[prec] * np.max(np.abs(v_ref))
 
 
 def test_user_lags_and_user_row_objective():
@@ -303,6 +303,39 @@ def test_concurrent_evaluations_match_alone():
     for gr in grids:
         gr.close()
     assert mixed == alone
+
+
+def _golden(name, seed):
+    import json
+    import os
+    p = os.path.join(os.path.dirname(__file__), "golden", f"{name}_seed{seed}.json")
+    with open(p) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("maker,prec", [(W.c3_precision, P.FP32_REFINE), (W.c3_precision, P.FP64),
+                                        (W.c4_gradient, P.FP32_REFINE)])
+def test_full_size_virtual_focus_against_oracle_values(maker, prec):
+    # The oracle's F and source-plane field for this design at full size (C3: 2500 cells,
+    # 20040 x 224, 4.5M unknowns) were written by tests/golden/make_golden.py, which runs
+    # only the oracle.  F within the stated tolerance (1e-8 FP32 + refinement, 1e-9 FP64),
+    # and v at the stored points within the same tolerance of the field's largest entry.
+    wl = maker()
+    gold = _golden(wl.name, 21)
+    ws = W.widths(wl.grid.n_cells, 21)
+    with P.Grid(wl.grid, prec=prec) as g:
+        g.set_design(ws)
+        g.factor()
+        F, info = g.avg_intensity(wl.objective, wl.light)
+        v_src, _ = g.solve_reciprocal(wl.objective)
+        v_src = _cplx(v_src)
+    assert gold["n_src"] == v_src.size
+    F_ref = gold["F"]
+    assert abs(F - F_ref) <= TOL_F[prec] * F_ref, (F, F_ref, info)
+    vg = np.array([complex(a, b) for a, b in gold["v"]])
+    vmax = np.max(np.abs(v_src))
+    assert np.max(np.abs(v_src[gold["v_idx"]] - vg)) <= TOL_F[prec] * vmax
+    assert abs(np.linalg.norm(v_src) - gold["v_norm2"]) <= TOL_F[prec] * gold["v_norm2"]
 
 
 @pytest.mark.parametrize("maker", [W.c3_precision, W.c4_gradient])

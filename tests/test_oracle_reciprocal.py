@@ -152,3 +152,19 @@ def test_virtual_focus_matches_on_grid_focus():
     # a downward (wrong-branch) propagator is far off
     K_bad = np.conj(K_all)
     assert abs(np.sum(K_bad * u[:, jm]) - got) / abs(got) > 0.1
+
+
+@pytest.mark.parametrize("maker", [W.c3_precision, W.c4_gradient])
+def test_virtual_focus_quadrature_converged_at_workload_heights(maker):
+    # The propagator integral at the heights the workloads use (C3: 990 rows with offsets
+    # up to 500 wavelengths; C4: 390 rows): doubling the panels and raising the order of
+    # the composite rule changes K by less than 1e-12 of its largest value, so the rule
+    # the library evaluates (256 panels x 32 points) sits on a converged integral.
+    wl = maker()
+    g = Grid(wl.grid)
+    dl = wl.objective.x_f - g.x_src()
+    sel = np.concatenate([dl[::max(1, dl.size // 300)], dl[[0, -1, dl.size // 2]]])
+    K = virtual_focus_kernel(g, sel, wl.objective.d_rows)
+    K_fine = virtual_focus_kernel(g, sel, wl.objective.d_rows, panels=512, order=48)
+    assert np.max(np.abs(K - K_fine)) < 1e-12 * np.max(np.abs(K_fine))
+    assert np.max(np.abs(dl)) > (400 if wl.objective.d_rows > 900 else 90)

@@ -81,3 +81,34 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
     assert float(out.item()) == -1.0
     with pytest.raises(P.RciError):
         P.qform_toeplitz_noalloc(v, lags, out)
+
+
+@pytest.mark.parametrize("n", [P.QFORM_NOALLOC_MAX_N, 1, 100])
+def test_noalloc_at_the_size_limits_of_its_scratch(lib, n):
+    # n = the maximum fills the scratch array to its last partial; n < 128 is a single,
+    # partial tile
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    v, lags = _inputs(n, 10 + n % 7)
+    ref = P.qform_toeplitz(v, lags)
+    out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    assert lib.rci_qform_toeplitz_noalloc(_ptr(v), _ptr(lags), n, _ptr(out), stream) == 0
+    torch.cuda.synchronize()
+    got = float(out.item())
+    assert abs(got - ref) <= TOL * abs(ref), (n, got, ref)
+
+
+def test_noalloc_binding_rejects_tensors_the_kernel_cannot_address(lib):
+    v, lags = _inputs(64, 5)
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        P.qform_toeplitz_noalloc(v, lags, torch.empty(1, dtype=torch.float64))   # host out
+    with pytest.raises(ValueError):
+        P.qform_toeplitz_noalloc(v.cpu(), lags, out)                             # host v
+    with pytest.raises(ValueError):
+        P.qform_toeplitz_noalloc(v, lags[:10].contiguous(), out)                 # short lags
+    with pytest.raises(ValueError):
+        P.qform_toeplitz_noalloc(v, lags, torch.empty(0, dtype=torch.float64, device="cuda"))
+    P.qform_toeplitz_noalloc(v, lags, out)
+    torch.cuda.synchronize()
+    ref = P.qform_toeplitz(v, lags)
+    assert abs(float(out.item()) - ref) <= TOL * abs(ref)

@@ -181,18 +181,33 @@ class Request:
     light: Light
     want_grad: bool
     seed: int
+    design_key: int = 0        # != 0: the server may keep the factorisation for a later request
 
 
 def serving_requests(n: int, rate_per_s: float, seed: int = 0, cells=(50, 1250), ny: int = 160,
-                     grad_fraction: float = 0.3, prec: int = PREC_FP32_REFINE) -> list:
+                     grad_fraction: float = 0.3, prec: int = PREC_FP32_REFINE,
+                     repeat_fraction: float = 0.0) -> list:
     """n requests with exponential inter-arrival times (mean 1/rate), each a seeded
-    metasurface of its own (design seed = seed * 1_000_003 + k)."""
+    metasurface of its own (design seed = seed * 1_000_003 + k).
+
+    With repeat_fraction > 0 every design carries a key (its seed + 1), and that fraction of
+    the requests (after the first) re-evaluate one of the last 32 designs -- same grid,
+    widths, objective and key -- under a new angular distribution, as a designer comparing
+    light sources on one metasurface would."""
     rng = np.random.default_rng(seed)
+    rep = np.random.default_rng(seed + 7_777_777)
     out = []
     t = 0.0
     lo, hi = math.log(cells[0]), math.log(cells[1])
     for k in range(n):
         t += rng.exponential(1.0 / rate_per_s) if rate_per_s > 0 else 0.0
+        if repeat_fraction > 0 and out and rep.uniform() < repeat_fraction:
+            src = out[-1 - int(rep.integers(0, min(32, len(out))))]
+            th1 = rep.uniform(5.0, 20.0)
+            light = Light(LIGHT_ANNULUS, th1=deg(th1), th2=deg(th1 + rep.uniform(5.0, 20.0)))
+            out.append(Request(t, src.grid, src.widths, src.objective, light,
+                               bool(rep.uniform() < grad_fraction), src.seed, src.design_key))
+            continue
         nc = int(round(math.exp(rng.uniform(lo, hi))))
         g = GridDesc(n_cells=nc, ny=ny, prec=prec)
         top = _pillar_top(g)
@@ -210,7 +225,8 @@ def serving_requests(n: int, rate_per_s: float, seed: int = 0, cells=(50, 1250),
             light = Light(LIGHT_ANNULUS, th1=deg(th1), th2=deg(th1 + rng.uniform(5.0, 20.0)))
         dseed = seed * 1_000_003 + k
         out.append(Request(t, g, widths(nc, dseed), obj, light,
-                           bool(rng.uniform() < grad_fraction), dseed))
+                           bool(rng.uniform() < grad_fraction), dseed,
+                           dseed + 1 if repeat_fraction > 0 else 0))
     return out
 
 
