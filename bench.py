@@ -141,11 +141,9 @@ def _replica_value(ws: int, steps: int, slowest_ms: float) -> float:
     return ws * steps / (slowest_ms * 1e-3)
 
 
-# DRAM bytes (read + write) per ny x ny block inverted by the FP32 look-ahead Gauss-Jordan
-# kernel, from one ncu capture of its 1010-block launch in the 200-wavelength factorisation
-# (207.0 MB read + 154.2 MB written; the kernel reads each block once and writes its inverse
-# once, 409.6 KB algorithmic).  Only valid for ny = 160 and that kernel as it stands.
-GJ_FP32_DRAM_BYTES_PER_BLOCK_NY160 = (206.989e6 + 154.217e6) / 1010
+# DRAM bytes (read + write) per ny x ny block inverted by the FP32 tensor-core Gauss-Jordan
+# kernel, from an ncu capture of the current kernel (None: no capture of it yet).
+GJ_TC_DRAM_BYTES_PER_BLOCK_NY160 = None
 # nominal dense TF32 / BF16 tensor rate (1.1 / 2.25 PFLOP/s)
 TF32_OVER_BF16 = 1.1 / 2.25
 
@@ -174,6 +172,26 @@ def _roofline(fam: str, stats: dict, prec: int, peaks: dict, peak_kind: str, ny:
                 "unit": "TFLOP/s", "frac": round(tflops / peak, 4), "traffic": None,
                 "kernel": fam, "peak_source": src + "; achieved counts the 3 TF32 products "
                 "per complex product"}
+    if fam == "invert" and prec != 0:
+        # FP32 blocks are inverted by the tensor-core Gauss-Jordan kernel: its rank-16
+        # updates run as 3xTF32 tcgen05 products (3x the algorithmic complex flops, as for the
+        # GEMMs); the 16-column panels in between are factored on the FP32 pipe
+        tflops = 3.0 * stats["flops"] / (ms * 1e-3) / 1e12
+        if live and live.get("tf32_tcgen05_tflops"):
+            peak = live["tf32_tcgen05_tflops"]
+            src = "measured in this run: tcgen05.mma kind::tf32 128x256 loop on every SM"
+        else:
+            peak = peaks.get("bf16_tflops_sustained", 1700.0) * TF32_OVER_BF16
+            src = f"{peak_kind} sustained bf16 x 1.1/2.25 (TF32)"
+        traffic = None
+        if ny == 160 and GJ_TC_DRAM_BYTES_PER_BLOCK_NY160:
+            blocks = stats["flops"] / (8.0 * ny ** 3)      # 8 ny^3 flops per block inverse
+            steps = max(1, stats.get("steps", 1))
+            traffic = round(GJ_TC_DRAM_BYTES_PER_BLOCK_NY160 * blocks / steps)
+        return {"bound": "tensor", "achieved": round(tflops, 3), "peak": round(peak, 1),
+                "unit": "TFLOP/s", "frac": round(tflops / peak, 4), "traffic": traffic,
+                "kernel": fam, "peak_source": src + "; achieved counts 3 TF32 products per "
+                "complex product (8 n^3 algorithmic flops per block)"}
     if fam in ("gemm", "invert", "level0", "qform"):
         tflops = stats["flops"] / (ms * 1e-3) / 1e12
         if prec == 0 or fam == "qform":
@@ -187,10 +205,6 @@ def _roofline(fam: str, stats: dict, prec: int, peaks: dict, peak_kind: str, ny:
             peak = SM_COUNT * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
             src = "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"
         traffic = None
-        if fam == "invert" and prec != 0 and ny == 160:
-            blocks = stats["flops"] / (8.0 * ny ** 3)      # 8 ny^3 flops per block inverse
-            steps = max(1, stats.get("steps", 1))
-            traffic = round(GJ_FP32_DRAM_BYTES_PER_BLOCK_NY160 * blocks / steps)
         return {"bound": "alu", "achieved": round(tflops, 4 if fam == "qform" else 3),
                 "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(tflops / peak, 4),
                 "traffic": traffic, "kernel": fam, "peak_source": src}

@@ -388,6 +388,19 @@ rci_status rci_profile_read(rci_grid* g, rci_profile* out);
 /* Kernels launched by this library in this process so far. */
 uint64_t rci_kernel_launches(void);
 
+/* Batched inversion of complex n x n blocks with partial pivoting (the block-inverse step of
+ * the factorisation behind rci_factor, exposed for reuse and testing; Sec. 4.1's single
+ * solve rests on it):  out[z] = src[z]^{-1},  z < batch.
+ * src, out: DEVICE arrays of batch row-major n x n blocks, contiguous, interleaved complex --
+ * complex64 for prec = RCI_FP32_REFINE, complex128 for RCI_FP64; must not overlap; src may
+ * be overwritten for n > 160.  kernel: 0 the factorisation's choice, 1 the SIMT Gauss-Jordan
+ * kernels, 2 the tensor-core Gauss-Jordan (FP32 and n <= 160 only: tcgen05 3xTF32 panel
+ * updates on the block held in tensor memory).  Pivot: largest |re| + |im| among the rows
+ * not yet used.  Synchronises `stream` (cudaStream_t or NULL) and allocates a 4-byte
+ * status word.  Errors: EINVAL, ESINGULAR (a zero pivot; out is then undefined), ETIMEOUT. */
+rci_status rci_block_inverse(const void* src, void* out, int64_t n, int64_t batch, int32_t prec,
+                             int32_t kernel, void* stream);
+
 /* Failure detection: every wait of a tensor-core pipeline stage (operand buffers,
  * accumulators) spins at most `cycles` SM clock cycles; a wait that runs out ends its
  * kernel (no trap), which records a device status that the next rci_factor / rci_solve

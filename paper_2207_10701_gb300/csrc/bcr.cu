@@ -999,8 +999,8 @@ cudaError_t launch_gj_cfg(cplx<T>* src, int64_t src_stride, cplx<T>* out, int64_
 // 256 with the register-panel kernel (shared memory while the block fits, else in place in
 // global memory); larger blocks with gj_inverse_kernel.
 template <typename T>
-cudaError_t launch_gj(cplx<T>* src, int64_t src_stride, cplx<T>* out, int64_t out_stride, int n,
-                      int batch, int32_t* status, cudaStream_t s) {
+cudaError_t launch_gj_simt(cplx<T>* src, int64_t src_stride, cplx<T>* out, int64_t out_stride,
+                           int n, int batch, int32_t* status, cudaStream_t s) {
   if (batch <= 0) return cudaSuccess;
   if (n > 1024) return cudaErrorInvalidValue;
   if constexpr (sizeof(T) == 4) {
@@ -1027,6 +1027,18 @@ cudaError_t launch_gj(cplx<T>* src, int64_t src_stride, cplx<T>* out, int64_t ou
     return launch_gj_cfg<T, false, 8, 5, 5, 256>(src, src_stride, out, out_stride, n, batch,
                                                  status, s);
   }
+}
+
+// Batched inverses: FP32 blocks of n <= 160 on the tensor cores (tc_gj.cu: blocked
+// Gauss-Jordan with tcgen05 panel updates, block in tensor memory); everything else with the
+// SIMT kernels above.
+template <typename T>
+cudaError_t launch_gj(cplx<T>* src, int64_t src_stride, cplx<T>* out, int64_t out_stride, int n,
+                      int batch, int32_t* status, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (n <= 160) return launch_tc_gj(src, src_stride, out, out_stride, n, batch, status, s);
+  }
+  return launch_gj_simt<T>(src, src_stride, out, out_stride, n, batch, status, s);
 }
 
 // ===================================================================== batched GEMM
@@ -2156,4 +2168,16 @@ cudaError_t bcr_solve(BcrHandle* h, const double2* cx, const void* b, void* x, i
   if (h->prec == RCI_FP64)
     return solve_t<double>(h, cx, (const double2*)b, (double2*)x, nrhs, s);
   return solve_t<float>(h, cx, (const float2*)b, (float2*)x, nrhs, s);
+}
+
+cudaError_t bcr_block_inverse(const void* src, void* out, int n, int batch, int prec, int kernel,
+                              int32_t* status, cudaStream_t s) {
+  const int64_t nn = (int64_t)n * n;
+  if (prec == RCI_FP64) {
+    if (kernel == 2) return cudaErrorInvalidValue;
+    return launch_gj<double>((double2*)src, nn, (double2*)out, nn, n, batch, status, s);
+  }
+  if (kernel == 1) return launch_gj_simt<float>((float2*)src, nn, (float2*)out, nn, n, batch, status, s);
+  if (kernel == 2) return launch_tc_gj((const float2*)src, nn, (float2*)out, nn, n, batch, status, s);
+  return launch_gj<float>((float2*)src, nn, (float2*)out, nn, n, batch, status, s);
 }

@@ -42,3 +42,9 @@ cudaError_t bcr_read_status(BcrHandle* h, int32_t* st, cudaStream_t s);
 int bcr_precision(const BcrHandle* h);
 // Optional profiler (owned by the caller) for the factor / solve kernel families.
 void bcr_set_profiler(BcrHandle* h, Profiler* p);
+
+// Batched inverse of complex n x n blocks (row-major, contiguous): prec as the handle's;
+// kernel 0 = the factorisation's choice, 1 = SIMT Gauss-Jordan, 2 = tensor-core Gauss-Jordan
+// (FP32, n <= 160).  A zero pivot is recorded in *status (device word).
+cudaError_t bcr_block_inverse(const void* src, void* out, int n, int batch, int prec, int kernel,
+                              int32_t* status, cudaStream_t s);

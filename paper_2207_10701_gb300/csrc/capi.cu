@@ -1163,6 +1163,28 @@ rci_status rci_set_refinement(rci_grid* g, double tol, int32_t max_steps) {
 
 uint64_t rci_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+rci_status rci_block_inverse(const void* src, void* out, int64_t n, int64_t batch, int32_t prec,
+                             int32_t kernel, void* stream) {
+  if (!src || !out || n < 1 || n > 1024 || batch < 1 || batch > (1 << 24) || kernel < 0 ||
+      kernel > 2 || (prec != RCI_FP64 && prec != RCI_FP32_REFINE))
+    return RCI_EINVAL;
+  if (kernel == 2 && (prec != RCI_FP32_REFINE || n > 160)) return RCI_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t* st = nullptr;
+  int32_t h = 0;
+  cudaError_t e = cudaMalloc((void**)&st, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(int32_t), s);
+  if (e == cudaSuccess) e = bcr_block_inverse(src, out, (int)n, (int)batch, prec, kernel, st, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, st, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(st);
+  if (e == cudaErrorInvalidValue) return RCI_EINVAL;
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? RCI_ENOMEM : RCI_ECUDA;
+  if (h == DEV_SINGULAR) return RCI_ESINGULAR;
+  if (h == DEV_TIMEOUT) return RCI_ETIMEOUT;
+  return RCI_OK;
+}
+
 int64_t rci_set_wait_limit(int64_t cycles) {
   const long long old = tc_wait_limit();
   tc_set_wait_limit((long long)cycles);

@@ -16,3 +16,10 @@ cudaError_t launch_tc_cgemm(int M, int N, int K, bool ta, bool tb, float2 alpha,
 // wait for the kernel's own MMAs before its tensor memory is freed always keeps the default.
 long long tc_wait_limit();
 void tc_set_wait_limit(long long cycles);
+
+// Batched inversion of complex FP32 n x n blocks (n <= 160) with partial pivoting, blocked
+// Gauss-Jordan with tensor-core (tcgen05, 3xTF32) panel updates; see tc_gj.cu.  src and out
+// are row-major, `stride` complex elements apart; src is not modified.  A zero pivot is
+// recorded as DEV_SINGULAR, an expired wait as DEV_TIMEOUT, in *status.
+cudaError_t launch_tc_gj(const float2* src, int64_t src_stride, float2* out, int64_t out_stride,
+                         int n, int batch, int32_t* status, cudaStream_t s);

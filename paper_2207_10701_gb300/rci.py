@@ -148,6 +148,7 @@ EXPORTED = {
     "rci_profile_read": (C.c_int, [_P, C.POINTER(ProfileC)]),
     "rci_kernel_launches": (C.c_uint64, []),
     "rci_set_wait_limit": (C.c_int64, [C.c_int64]),
+    "rci_block_inverse": (C.c_int, [_P, _P, C.c_int64, C.c_int64, C.c_int32, C.c_int32, _P]),
     "rci_measure_peaks": (C.c_int, [C.c_int, C.POINTER(PeaksC)]),
     "rci_status_str": (C.c_char_p, [C.c_int]),
     "rci_last_error": (C.c_char_p, [_P]),
@@ -421,6 +422,23 @@ def measure_peaks(device: int = 0) -> dict:
     p = PeaksC()
     _check(lib().rci_measure_peaks(device, C.byref(p)))
     return {n: getattr(p, n) for n, _ in PeaksC._fields_ if n != "reserved"}
+
+
+def block_inverse(blocks, kernel: int = 0, stream=None):
+    """Inverses of a batch of complex blocks (CUDA tensor [batch, n, n], complex64 or
+    complex128) with the factorisation's block-inverse kernels (rci_block_inverse);
+    kernel 0 = its choice, 1 = SIMT, 2 = tensor cores (complex64, n <= 160)."""
+    torch = _torch()
+    if blocks.dim() != 3 or blocks.shape[1] != blocks.shape[2] or not blocks.is_cuda:
+        raise ValueError("blocks: CUDA tensor [batch, n, n]")
+    if blocks.dtype not in (torch.complex64, torch.complex128):
+        raise TypeError("complex64 or complex128 blocks")
+    src = blocks.contiguous().clone()
+    out = torch.empty_like(src)
+    prec = FP32_REFINE if src.dtype == torch.complex64 else FP64
+    _check(lib().rci_block_inverse(_dptr(src), _dptr(out), src.shape[1], src.shape[0], prec,
+                                   kernel, _stream(stream)))
+    return out
 
 
 def set_wait_limit(cycles: int) -> int:

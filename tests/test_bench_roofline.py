@@ -17,30 +17,30 @@ PEAKS = {"hbm_gbs": 6772.0, "bf16_tflops": 1962.0, "bf16_tflops_sustained": 1723
          "sm_max_mhz": 2070.0}
 
 
-def test_invert_record_counts_flops_and_scales_traffic_by_blocks():
+def test_invert_record_counts_flops_against_the_tensor_rate():
     ny, blocks, steps = 160, 2020, 20
     flops = 8.0 * ny ** 3 * blocks * steps            # complex Gauss-Jordan: 8 n^3 per block
-    ms = 5.7 * steps
+    ms = 3.3 * steps
     r = bench._roofline("invert", {"ms": ms, "flops": flops, "bytes": 0.0, "steps": steps},
-                        1, PEAKS, "measured", ny=ny)
-    achieved = flops / (ms * 1e-3) / 1e12
-    peak = 152 * 128 * 2 * 2070.0e6 / 1e12
-    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["kernel"] == "invert"
+                        1, PEAKS, "measured", ny=ny, live={"tf32_tcgen05_tflops": 1200.0})
+    achieved = 3 * flops / (ms * 1e-3) / 1e12         # 3xTF32 tensor products
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s" and r["kernel"] == "invert"
     assert r["achieved"] == pytest.approx(achieved, abs=1e-3)
-    assert r["peak"] == pytest.approx(peak, abs=1e-2)
-    assert r["frac"] == pytest.approx(achieved / peak, abs=1e-4)
-    # traffic per evaluation: the captured bytes per block times the blocks of one evaluation
-    assert r["traffic"] == round(bench.GJ_FP32_DRAM_BYTES_PER_BLOCK_NY160 * blocks)
-    # each block is read once and its inverse written once: the captured bytes lie between
-    # the reads alone and reads plus writes (writes still in L2 at kernel end are not counted)
-    per_block = bench.GJ_FP32_DRAM_BYTES_PER_BLOCK_NY160
-    assert 8 * ny * ny <= per_block <= 2 * 8 * ny * ny * 1.01
+    assert r["peak"] == 1200.0
+    assert r["frac"] == pytest.approx(achieved / 1200.0, abs=1e-4)
+    if bench.GJ_TC_DRAM_BYTES_PER_BLOCK_NY160:
+        assert r["traffic"] == round(bench.GJ_TC_DRAM_BYTES_PER_BLOCK_NY160 * blocks)
+        # each block is read once and its inverse written once
+        assert 8 * ny * ny <= bench.GJ_TC_DRAM_BYTES_PER_BLOCK_NY160 <= 2 * 8 * ny * ny * 1.01
+    else:
+        assert r["traffic"] is None
 
 
-def test_invert_traffic_only_for_the_captured_kernel():
+def test_fp64_invert_record_is_held_against_the_fp64_rate():
     stats = {"ms": 10.0, "flops": 8.0 * 96 ** 3 * 10, "bytes": 0.0, "steps": 1}
-    assert bench._roofline("invert", stats, 1, PEAKS, "measured", ny=96)["traffic"] is None
-    assert bench._roofline("invert", stats, 0, PEAKS, "measured", ny=160)["traffic"] is None
+    r = bench._roofline("invert", stats, 0, PEAKS, "measured", ny=160,
+                        live={"fp64_fma_tflops": 1.05})
+    assert r["bound"] == "alu" and r["peak"] == 1.05 and r["traffic"] is None
 
 
 def test_fp32_gemm_record_is_held_against_the_tf32_tensor_rate():
@@ -95,7 +95,9 @@ def test_measured_peaks_of_the_run_replace_the_derived_ones():
     assert g["peak"] == 1000.0 and "measured in this run" in g["peak_source"]
     assert g["frac"] == pytest.approx(300.0 / 1000.0, rel=1e-3)
     inv = bench._roofline("invert", st, 1, PEAKS, "measured", ny=96, live=live)
-    assert inv["peak"] == 70.0 and inv["frac"] == pytest.approx(100.0 / 70.0, rel=1e-3)
+    assert inv["peak"] == 1000.0 and inv["bound"] == "tensor"
+    lvl = bench._roofline("level0", st, 1, PEAKS, "measured", live=live)
+    assert lvl["peak"] == 70.0 and lvl["frac"] == pytest.approx(100.0 / 70.0, rel=1e-3)
     g64 = bench._roofline("gemm", st, 0, PEAKS, "measured", live=live)
     assert g64["peak"] == 1.1
     q = bench._roofline("qform", st, 1, PEAKS, "measured", live=live)
