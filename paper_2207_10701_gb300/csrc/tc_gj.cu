@@ -220,13 +220,22 @@ __device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, lon
   }
 }
 
-// 1 / (re + i im) with the scaling of crecip, from two correctly rounded reciprocals
-__device__ __forceinline__ float2 crecip_rcp(float re, float im) {
+// 1 / (re + i im) = (re - i im) / (re^2 + im^2).  Both parts are scaled by the power of two
+// that brings the larger magnitude into [1, 2) (exact), so d = ar^2 + ai^2 lies in [1, 8);
+// 1 / d is the hardware approximation refined by one Newton step r <- r + r (1 - d r), and
+// the result is scaled back.  Returns 0 when the larger magnitude is below 1e-37 (a zero
+// pivot in FP32 terms) or not finite.
+__device__ __forceinline__ float2 crecip_fast(float re, float im) {
   const float s = fmaxf(fabsf(re), fabsf(im));
-  if (!(s > 0.f)) return make_float2(0.f, 0.f);
-  const float is = __frcp_rn(s);
-  const float ar = re * is, ai = im * is;
-  const float q = __frcp_rn(fmaf(ar, ar, ai * ai)) * is;
+  if (!(s > 1e-37f) || !(s < 1e37f)) return make_float2(0.f, 0.f);
+  const uint32_t e = __float_as_uint(s) & 0x7F800000u;
+  const float sc = __uint_as_float(0x7F000000u - e);   // 2^-(exponent of s), exact
+  const float ar = re * sc, ai = im * sc;
+  const float d = fmaf(ar, ar, ai * ai);
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+  r = fmaf(r, fmaf(-d, r, 1.f), r);
+  const float q = r * sc;
   return make_float2(ar * q, -ai * q);
 }
 
@@ -519,10 +528,7 @@ __global__ void __launch_bounds__(GJT_THREADS, 1) tc_gj_kernel(GjtArgs p) {
             const unsigned long long v = pslot[b];
             const int P = 255 - (int)(v & 255ull);
             const int W = P < 128 ? (P >> 5) : 4 + ((P - 128) >> 4);
-            if (tid == 0) {
-              piv[k] = P;
-              if (((uint32_t)v >> 8) == 0u) sing = true;
-            }
+            if (tid == 0) piv[k] = P;
             float rr[16], ri[16];
             const float4* rb = reinterpret_cast<const float4*>(rowbuf + (b * GJT_PWARPS + W) * 16);
 #pragma unroll
@@ -533,7 +539,9 @@ __global__ void __launch_bounds__(GJT_THREADS, 1) tc_gj_kernel(GjtArgs p) {
               rr[2 * q + 1] = x4.z;
               ri[2 * q + 1] = x4.w;
             }
-            const float2 pinv = crecip_rcp(rr[u], ri[u]);
+            const float2 pinv = crecip_fast(rr[u], ri[u]);
+            if (tid == 0 && (((uint32_t)v >> 8) == 0u || (pinv.x == 0.f && pinv.y == 0.f)))
+              sing = true;
             // pivot row: row / pivot with 1 / pivot in the pivot column; other rows:
             // x - (x_u / pivot) row with -x_u / pivot in the pivot column
             const bool isp = !used && row == P;
