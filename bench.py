@@ -246,6 +246,58 @@ def _cpu_baseline(seed: int, timeout_s: float = 240.0):
                       "single thread, on the design of the first timed GPU evaluation"}, d["F"]
 
 
+def _bf_worker(args):
+    """One host process of the oracle brute-force timing: factor design `seed` of the 200-
+    wavelength workload, then the forward solves of its share of the 1000-angle rule."""
+    seed, worker, workers, per = args
+    import workloads as W
+    from oracle.light import quadrature_rule
+    from oracle.reciprocal import Evaluation
+    wl = W.c2_collimator()
+    t0 = time.perf_counter()
+    ev = Evaluation(wl, W.widths(wl.grid.n_cells, seed))
+    t1 = time.perf_counter()
+    theta, _ = quadrature_rule(wl.light, wl.n_angles)
+    ev.fom_per_angle(theta[worker::workers][:per])
+    return t1 - t0, time.perf_counter() - t1, per
+
+
+def _cpu_bruteforce(seed: int, per_worker: int = 4, max_workers: int = 8):
+    """The oracle's brute-force average (Eq. 6, Sec. 5.2) timed on the host cores: one
+    spawned process per core (up to max_workers), each factoring the design once and solving
+    per_worker angles of the 1000-angle rule; reports the measured rates and the time 1000
+    angles would take on those cores."""
+    import multiprocessing as mp
+    workers = max(1, min(max_workers, os.cpu_count() or 1))
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                            "MKL_NUM_THREADS", "CUDA_VISIBLE_DEVICES")}
+    for k in saved:
+        os.environ[k] = "" if k == "CUDA_VISIBLE_DEVICES" else "1"
+    try:
+        ctx = mp.get_context("spawn")
+        t0 = time.perf_counter()
+        with ctx.Pool(workers) as pool:
+            res = pool.map(_bf_worker, [(seed, w, workers, per_worker) for w in range(workers)])
+        wall = time.perf_counter() - t0
+    except Exception as e:  # noqa: BLE001
+        return {"kind": "oracle", "sample": f"failed: {type(e).__name__}: {e}"}
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    fac = statistics.mean(r[0] for r in res)
+    per_angle = statistics.mean(r[1] / r[2] for r in res)
+    n = sum(r[2] for r in res)
+    return {"kind": "oracle", "cores": workers, "angles_sampled": n, "wall_s": round(wall, 2),
+            "factor_s": round(fac, 2), "s_per_angle_per_core": round(per_angle, 3),
+            "angles_1000_s_extrapolated": round(fac + 1000 / workers * per_angle, 1),
+            "sample": f"{workers} processes x {per_worker} angles of the 1000-angle rule on the "
+                      "200-wavelength workload, each process factoring the design once "
+                      "(SuperLU, single thread) and refining every solve (double-double)"}
+
+
 def _golden(name: str, seed: int):
     """The oracle's stored values for a full-size design (written by tests/golden/
     make_golden.py, which runs only the oracle), or None."""
@@ -584,6 +636,8 @@ def run_ours(args):
         # the oracle on the design of the first timed evaluation: its time is the CPU
         # baseline, its F the per-result error of that evaluation
         cb, F_or = _cpu_baseline(Wm)
+        if not args.quick:
+            cb["bruteforce"] = _cpu_bruteforce(Wm)
         line["cpu_baseline"] = cb
         if F_or is not None:
             line["rel_err_vs_oracle"] = {"F_gpu": Fs[0], "F_oracle": F_or,
@@ -650,6 +704,9 @@ def _serve_stream(P, W, local, n_requests, burst, slots, arena_gb, cache_gb, rep
     wait = np.array([(r["t_start_us"] - r["t_submit_us"]) * 1e-3 for r in res])
     ok = [r["status"] == 0 for r in res]             # converged to the tolerance
     unconverged = sum(1 for r in res if r["status"] == 6)   # RCI_ENOCONV: value not counted
+    status_counts = {}
+    for r in res:
+        status_counts[str(r["status"])] = status_counts.get(str(r["status"]), 0) + 1
     span = (max(r["t_end_us"] for r in res) - min(r["t_submit_us"] for r in res)) * 1e-6
     grad = np.array([q.want_grad for q in reqs])
     delta = ("submitted", "completed", "failed", "admission_waits", "bypasses", "cache_hits",
@@ -662,7 +719,7 @@ def _serve_stream(P, W, local, n_requests, burst, slots, arena_gb, cache_gb, rep
         "p99_queue_ms": round(float(np.percentile(wait, 99)), 3),
         "p50_ms_gradient": round(float(np.percentile(lat[grad], 50)), 3) if grad.any() else None,
         "requests": len(reqs), "failed": len(reqs) - sum(ok), "unconverged": unconverged,
-        "repeated_designs": round(repeat, 3),
+        "status_counts": status_counts, "repeated_designs": round(repeat, 3),
         "arrival_rate_per_s": round(rate, 3), "capacity_evals_per_s": round(capacity, 3),
         "config": {"workload": "serving stream: 50-1250 cells log-uniform, ny 160, "
                                "concentrator/collimator, cone/annulus, 30% gradient",

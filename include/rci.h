@@ -121,6 +121,11 @@ typedef struct {
   double ms_factor;      /* device time of the last factorisation */
   double ms_solve;       /* device time of the last solve incl. refinement */
   double ms_qform;       /* device time of the last quadratic form */
+  double growth_est;     /* growth estimate of the factorisation used: the largest |re|, |im|
+                            among the diagonal blocks it inverted (the Schur complements of every
+                            reduction level) over the largest among A's coefficients.  Block
+                            cyclic reduction pivots only inside blocks, so large values flag a
+                            factorisation whose rounding errors refinement must absorb. */
 } rci_info;
 
 typedef struct rci_grid rci_grid;

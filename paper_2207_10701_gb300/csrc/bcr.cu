@@ -1,5 +1,6 @@
 // Block cyclic reduction factor and solve (see bcr.cuh for the algebra).
 #include <algorithm>
+#include <cstring>
 #include <new>
 #include <vector>
 
@@ -1032,13 +1033,55 @@ cudaError_t launch_gj_simt(cplx<T>* src, int64_t src_stride, cplx<T>* out, int64
 // Batched inverses: FP32 blocks of n <= 160 on the tensor cores (tc_gj.cu: blocked
 // Gauss-Jordan with tcgen05 panel updates, block in tensor memory); everything else with the
 // SIMT kernels above.
+// Largest |re|, |im| over `batch` n x n blocks (stride in elements) into *maxabs (float bits,
+// atomicMax), for the growth estimate of the SIMT paths (the tensor-core kernel records it
+// while it reads its blocks).
+template <typename T>
+__global__ void block_maxabs_kernel(const cplx<T>* __restrict__ a, int64_t stride, int64_t nn,
+                                    int batch, uint32_t* maxabs) {
+  float m = 0.f;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nn * batch;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t z = e / nn;
+    const cplx<T> v = a[z * stride + (e - z * nn)];
+    m = fmaxf(m, (float)fmax(fabs(v.x), fabs(v.y)));
+  }
+  const uint32_t wm = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+  if ((threadIdx.x & 31) == 0) atomicMax(maxabs, wm);
+}
+
 template <typename T>
 cudaError_t launch_gj(cplx<T>* src, int64_t src_stride, cplx<T>* out, int64_t out_stride, int n,
-                      int batch, int32_t* status, cudaStream_t s) {
+                      int batch, int32_t* status, cudaStream_t s, uint32_t* maxabs = nullptr) {
+  if (batch <= 0) return cudaSuccess;
   if constexpr (sizeof(T) == 4) {
-    if (n <= 160) return launch_tc_gj(src, src_stride, out, out_stride, n, batch, status, s);
+    if (n <= 160)
+      return launch_tc_gj(src, src_stride, out, out_stride, n, batch, status, s, maxabs);
+  }
+  if (maxabs) {
+    const int64_t nn = (int64_t)n * n;
+    const int64_t tot = nn * batch;
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(tot, 256), 4 * 152);
+    block_maxabs_kernel<T><<<grid, 256, 0, s>>>(src, src_stride, nn, batch, maxabs);
+    rci_note_launch();
+    RCI_CUDA_TRY(cudaGetLastError());
   }
   return launch_gj_simt<T>(src, src_stride, out, out_stride, n, batch, status, s);
+}
+
+// Largest |re|, |im| of the operator's coefficients (diagonal and couplings)
+__global__ void coeff_maxabs_kernel(const double2* __restrict__ dg, const double2* __restrict__ cx,
+                                    const double2* __restrict__ cy, int64_t N, uint32_t* maxabs) {
+  float m = 0.f;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double2 a = dg[e], b = cx[e], c = cy[e];
+    const double v = fmax(fmax(fmax(fabs(a.x), fabs(a.y)), fmax(fabs(b.x), fabs(b.y))),
+                          fmax(fabs(c.x), fabs(c.y)));
+    m = fmaxf(m, (float)v);
+  }
+  const uint32_t wm = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+  if ((threadIdx.x & 31) == 0) atomicMax(maxabs, wm);
 }
 
 // ===================================================================== batched GEMM
@@ -1860,7 +1903,7 @@ cudaError_t bcr_create(int nx, int ny, int prec, const DevMem* mem, BcrHandle** 
     alloc(&h->Lw[i], (size_t)n1 * nn * h->esz);
   }
   alloc(&h->store, (size_t)store_elems * h->esz);
-  alloc((void**)&h->status, sizeof(int32_t));
+  alloc((void**)&h->status, 3 * sizeof(int32_t));  // status, max |A|, max |inverted block| (bits)
   if (e != cudaSuccess) {
     bcr_destroy(h);
     return e;
@@ -1870,9 +1913,18 @@ cudaError_t bcr_create(int nx, int ny, int prec, const DevMem* mem, BcrHandle** 
   return cudaSuccess;
 }
 
-cudaError_t bcr_read_status(BcrHandle* h, int32_t* st, cudaStream_t s) {
-  RCI_CUDA_TRY(cudaMemcpyAsync(st, h->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  return cudaStreamSynchronize(s);
+cudaError_t bcr_read_status(BcrHandle* h, int32_t* st, cudaStream_t s, double* growth) {
+  uint32_t w[3] = {0, 0, 0};
+  RCI_CUDA_TRY(cudaMemcpyAsync(w, h->status, sizeof(w), cudaMemcpyDeviceToHost, s));
+  RCI_CUDA_TRY(cudaStreamSynchronize(s));
+  *st = (int32_t)w[0];
+  if (growth) {
+    float a, d;
+    std::memcpy(&a, &w[1], 4);
+    std::memcpy(&d, &w[2], 4);
+    *growth = a > 0.f ? (double)d / (double)a : 0.0;
+  }
+  return cudaSuccess;
 }
 
 template <typename T>
@@ -1882,7 +1934,15 @@ static cudaError_t factor_t(BcrHandle* h, const double2* dg, const double2* cx, 
   const int64_t nn = (int64_t)ny * ny;
   const int m0 = (int)h->m[0];
   const int n1 = (nx + 1) / 2;
-  RCI_CUDA_TRY(cudaMemsetAsync(h->status, 0, sizeof(int32_t), s));
+  RCI_CUDA_TRY(cudaMemsetAsync(h->status, 0, 3 * sizeof(int32_t), s));
+  uint32_t* maxabs = reinterpret_cast<uint32_t*>(h->status) + 1;
+  {
+    const int64_t N = (int64_t)nx * ny;
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(N, 256), 4 * 152);
+    coeff_maxabs_kernel<<<grid, 256, 0, s>>>(dg, cx, cy, N, maxabs);
+    rci_note_launch();
+    RCI_CUDA_TRY(cudaGetLastError());
+  }
   auto tdl = (cplx<T>*)h->tdl;
   auto tdinv = (cplx<T>*)h->tdinv;
   auto tdu = (cplx<T>*)h->tdu;
@@ -1929,7 +1989,7 @@ static cudaError_t factor_t(BcrHandle* h, const double2* dg, const double2* cx, 
     // D_r^{-1} for the odd rows (the working copy of D_r is destroyed)
     {
       ProfScope ps(h->prof, PF_INVERT, s, 8.0 * ny * (double)nn * m, 2.0 * m * nn * sizeof(cplx<T>), 1);
-      RCI_CUDA_TRY(launch_gj<T>(D + nn, 2 * nn, Dinv, nn, ny, m, h->status, s));
+      RCI_CUDA_TRY(launch_gj<T>(D + nn, 2 * nn, Dinv, nn, ny, m, h->status, s, maxabs + 1));
     }
     // X_k = Dinv_k L_{2k+1};  Y_k = Dinv_k L_{2k+2}^T
     RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, false, one, Dinv, ny, nn, L + nn, ny, 2 * nn, zero,
@@ -1950,7 +2010,8 @@ static cudaError_t factor_t(BcrHandle* h, const double2* dg, const double2* cx, 
   // last single row
   {
     ProfScope ps(h->prof, PF_INVERT, s, 8.0 * ny * (double)nn, 2.0 * nn * sizeof(cplx<T>), 1);
-    RCI_CUDA_TRY(launch_gj<T>((cplx<T>*)h->Dw[cur], 0, store + h->final_off, 0, ny, 1, h->status, s));
+    RCI_CUDA_TRY(launch_gj<T>((cplx<T>*)h->Dw[cur], 0, store + h->final_off, 0, ny, 1, h->status, s,
+                              maxabs + 1));
   }
   return cudaSuccess;
 }

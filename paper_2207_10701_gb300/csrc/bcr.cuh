@@ -37,8 +37,10 @@ cudaError_t bcr_factor(BcrHandle* h, const double2* dg, const double2* cx, const
 // handle's precision (float2 or double2 buffers).  b and x must not overlap.
 cudaError_t bcr_solve(BcrHandle* h, const double2* cx, const void* b, void* x, int nrhs,
                       cudaStream_t s);
-// Device status word (DEV_OK / DEV_SINGULAR / DEV_NONFINITE), read synchronously.
-cudaError_t bcr_read_status(BcrHandle* h, int32_t* st, cudaStream_t s);
+// Device status word (DEV_OK / DEV_SINGULAR / DEV_NONFINITE), read synchronously; with
+// growth, also the growth estimate of the last factorisation: the largest |re|, |im| of the
+// blocks it inverted (the Schur complements of every level) over that of A's coefficients.
+cudaError_t bcr_read_status(BcrHandle* h, int32_t* st, cudaStream_t s, double* growth = nullptr);
 int bcr_precision(const BcrHandle* h);
 // Optional profiler (owned by the caller) for the factor / solve kernel families.
 void bcr_set_profiler(BcrHandle* h, Profiler* p);

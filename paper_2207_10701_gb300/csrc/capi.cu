@@ -56,6 +56,8 @@ struct rci_grid {
   bool use64 = false;
   double2* corr64 = nullptr;
   int64_t corr64_n = 0;
+  DevMem mem64;  // where the fallback's buffers came from (cudaMalloc when the grid's own
+                 // memory source, e.g. a serving arena, had no room left for them)
   // correlated-light inputs (theta, weights, C, alpha) and multi-output results (grown on demand)
   void* cbuf = nullptr;
   size_t cbuf_bytes = 0;
@@ -71,6 +73,7 @@ struct rci_grid {
   double tol32 = 1e-10, tol64 = 1e-13;
   int max_refine32 = 31, max_refine64 = 2;  // FP32: solves, the first one included
   size_t bytes = 0;
+  double growth = 0.0, growth64 = 0.0;  // growth estimates of the factorisations (FP32/FP64)
   cudaEvent_t ev[6] = {};
   Profiler prof;
   std::string err;
@@ -323,12 +326,19 @@ rci_status solve64(rci_grid* g, BcrHandle* h, const double2* b, double2* x, doub
 rci_status fp64_fallback(rci_grid* g) {
   if (g->use64) return RCI_OK;
   if (!g->bcr64) {
-    CK(bcr_create(g->g.nx, g->g.ny, RCI_FP64, &g->mem, &g->bcr64, nullptr), "FP64 fallback store");
+    // The fallback is not part of a grid's admitted footprint: when the grid's memory source
+    // (a serving arena) is full, the FP64 store comes from cudaMalloc instead.
+    cudaError_t e = bcr_create(g->g.nx, g->g.ny, RCI_FP64, &g->mem, &g->bcr64, nullptr);
+    if (e == cudaErrorMemoryAllocation && g->mem.alloc_fn) {
+      (void)cudaGetLastError();
+      e = bcr_create(g->g.nx, g->g.ny, RCI_FP64, nullptr, &g->bcr64, nullptr);
+    }
+    CK(e, "FP64 fallback store");
     bcr_set_profiler(g->bcr64, &g->prof);
   }
   CK(bcr_factor(g->bcr64, g->dg, g->cx, g->cy, g->s), "FP64 fallback factor");
   int32_t st = 0;
-  CK(bcr_read_status(g->bcr64, &st, g->s), "FP64 fallback status");
+  CK(bcr_read_status(g->bcr64, &st, g->s, &g->growth64), "FP64 fallback status");
   if (st == DEV_SINGULAR) return fail(g, RCI_ESINGULAR, "zero pivot in a diagonal block (FP64)");
   g->use64 = true;
   return RCI_OK;
@@ -336,10 +346,17 @@ rci_status fp64_fallback(rci_grid* g) {
 
 rci_status ensure_corr64(rci_grid* g, int64_t n) {
   if (g->corr64_n >= n) return RCI_OK;
-  dfree(g, g->corr64);
+  g->mem64.release(g->corr64);
   g->corr64 = nullptr;
   g->corr64_n = 0;
-  CK(dalloc(g, &g->corr64, sizeof(double2) * n), "FP64 fallback correction");
+  g->mem64 = g->mem;
+  cudaError_t e = g->mem64.alloc((void**)&g->corr64, sizeof(double2) * n);
+  if (e == cudaErrorMemoryAllocation && g->mem.alloc_fn) {
+    (void)cudaGetLastError();
+    g->mem64 = DevMem{};
+    e = g->mem64.alloc((void**)&g->corr64, sizeof(double2) * n);
+  }
+  CK(e, "FP64 fallback correction");
   g->corr64_n = n;
   return RCI_OK;
 }
@@ -401,6 +418,7 @@ rci_status refined_solve(rci_grid* g, const double2* b, double2* x, double2* r, 
     info->refine_iters = it;
     info->rel_residual = worst;
     info->fallback = fell_back ? 1 : 0;
+    info->growth_est = fell_back ? g->growth64 : g->growth;
   }
   if (nrhs > 1) {  // the multi-RHS solve runs tensor-core GEMMs with bounded waits
     int32_t dst = 0;
@@ -462,6 +480,7 @@ rci_status run_angles(rci_grid* g, const rci_objective* o, const double* th_dev,
   if (info) {
     info->refine_iters = worst_it;
     info->rel_residual = worst_res;
+    info->growth_est = g->use64 ? g->growth64 : g->growth;
   }
   return agg;
 }
@@ -523,8 +542,9 @@ void destroy_grid(rci_grid* g, bool sync) {
   void* ps[] = {g->widths, g->eps, g->dg, g->cx, g->cy, g->dg0, g->kss, g->b1, g->x1, g->r1, g->r32, g->d32,
                 g->crow, g->vsrc, g->lags, g->qpart, g->dscal, g->part_r, g->part_b, g->ratio,
                 g->vf_scratch, g->dstatus, g->mb, g->mx, g->mr, g->m32a, g->m32b, g->th_d,
-                g->wq_d, g->f_d, g->mu, g->gsrc, g->tpart, g->dgrad, g->corr64, g->cbuf, g->mF};
+                g->wq_d, g->f_d, g->mu, g->gsrc, g->tpart, g->dgrad, g->cbuf, g->mF};
   for (void* p : ps) dfree(g, p);
+  g->mem64.release(g->corr64);
   bcr_destroy(g->bcr);
   bcr_destroy(g->bcr64);
   if (g->prof.pool) {
@@ -762,7 +782,7 @@ rci_status rci_factor(rci_grid* g) {
   CK(cudaEventRecord(g->ev[1], g->s), "event");
   int32_t st = 0, sd = 0;
   CK(cudaMemcpyAsync(&sd, g->dstatus, sizeof(int32_t), cudaMemcpyDeviceToHost, g->s), "status");
-  CK(bcr_read_status(g->bcr, &st, g->s), "factor status");
+  CK(bcr_read_status(g->bcr, &st, g->s, &g->growth), "factor status");
   if (g->prof.on) g->prof.collect();
   if (sd == DEV_BADINPUT) {
     g->has_design = false;
@@ -912,6 +932,7 @@ rci_status rci_avg_intensity_grad(rci_grid* g, const rci_objective* obj, const r
     info->refine_iters = i1.refine_iters > i2.refine_iters ? i1.refine_iters : i2.refine_iters;
     info->rel_residual = i1.rel_residual > i2.rel_residual ? i1.rel_residual : i2.rel_residual;
     info->fallback = i1.fallback | i2.fallback;
+    info->growth_est = i2.growth_est > i1.growth_est ? i2.growth_est : i1.growth_est;
     float ms = 0;
     cudaEventElapsedTime(&ms, g->ev[2], g->ev[3]);
     info->ms_solve = i1.ms_solve + ms;
@@ -1048,6 +1069,7 @@ rci_status rci_avg_intensity_multi(rci_grid* g, const rci_objective* objs, int64
     info->refine_iters = worst_it;
     info->rel_residual = worst_res;
     info->fallback = fb;
+    info->growth_est = g->use64 ? g->growth64 : g->growth;
   }
   return agg;
 }

@@ -20,6 +20,8 @@ void tc_set_wait_limit(long long cycles);
 // Batched inversion of complex FP32 n x n blocks (n <= 160) with partial pivoting, blocked
 // Gauss-Jordan with tensor-core (tcgen05, 3xTF32) panel updates; see tc_gj.cu.  src and out
 // are row-major, `stride` complex elements apart; src is not modified.  A zero pivot is
-// recorded as DEV_SINGULAR, an expired wait as DEV_TIMEOUT, in *status.
+// recorded as DEV_SINGULAR, an expired wait as DEV_TIMEOUT, in *status.  maxabs (or null):
+// atomicMax of the bit pattern of the largest |re|, |im| among the blocks' entries.
 cudaError_t launch_tc_gj(const float2* src, int64_t src_stride, float2* out, int64_t out_stride,
-                         int n, int batch, int32_t* status, cudaStream_t s);
+                         int n, int batch, int32_t* status, cudaStream_t s,
+                         uint32_t* maxabs = nullptr);

@@ -252,6 +252,7 @@ struct GjtArgs {
   int32_t* status;
   long long wait_limit;
   int vec16;            // 1: rows may be copied in 16-byte pieces (n even, 16-byte aligned)
+  uint32_t* maxabs;     // or null: atomicMax of the bits of the largest |re|, |im| read
 };
 
 // Threads and rows: panel warps 0-3 own complex rows r = 32 w + lane (tiles 0 and 1, their
@@ -365,6 +366,7 @@ __global__ void __launch_bounds__(GJT_THREADS, 1) tc_gj_kernel(GjtArgs p) {
     __syncthreads();
     // ------------------------------------------------ staging -> tensor memory
     if (main_warp) {
+      float amax = 0.f;
       for (int c0 = 0; c0 < np; c0 += 16) {
         float re[16], im[16];
 #pragma unroll
@@ -375,9 +377,16 @@ __global__ void __launch_bounds__(GJT_THREADS, 1) tc_gj_kernel(GjtArgs p) {
           im[2 * q] = v.y;
           re[2 * q + 1] = v.z;
           im[2 * q + 1] = v.w;
+          amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
         }
         tmem_st16(taddr(0, c0), re);
         tmem_st16(taddr(1, c0), im);
+      }
+      // the largest magnitude of the block (rows 128 .. 159 are read by warps 4-5 as well,
+      // but those are covered here too: warps 0-3 see every row < 128, the tile-2 warps below)
+      if (p.maxabs) {
+        const uint32_t m = __reduce_max_sync(0xffffffffu, __float_as_uint(amax));
+        if (l == 0) atomicMax(p.maxabs, m);
       }
     } else if (!mma_warp && T == 3) {
       for (int c0 = 0; c0 < np; c0 += 16) {
@@ -390,6 +399,15 @@ __global__ void __launch_bounds__(GJT_THREADS, 1) tc_gj_kernel(GjtArgs p) {
           y[2 * q + 1] = part ? v.w : v.z;
         }
         tmem_st16(taddr(2, c0), y);
+      }
+      if (p.maxabs) {
+        float amax = 0.f;
+        for (int c0 = 0; tile2_lane && part == 0 && c0 < np; c0 += 2) {
+          const float4 v = *reinterpret_cast<const float4*>(stage + row * SLD + 2 * c0);
+          amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+        }
+        const uint32_t m = __reduce_max_sync(0xffffffffu, __float_as_uint(amax));
+        if (l == 0) atomicMax(p.maxabs, m);
       }
     }
     tmem_wait_st();
@@ -791,7 +809,7 @@ __global__ void __launch_bounds__(GJT_THREADS, 1) tc_gj_kernel(GjtArgs p) {
 }  // namespace
 
 cudaError_t launch_tc_gj(const float2* src, int64_t src_stride, float2* out, int64_t out_stride,
-                         int n, int batch, int32_t* status, cudaStream_t s) {
+                         int n, int batch, int32_t* status, cudaStream_t s, uint32_t* maxabs) {
   if (batch <= 0) return cudaSuccess;
   if (n < 1 || n > GJT_NMAX) return cudaErrorInvalidValue;
   static const cudaError_t attr = cudaFuncSetAttribute(
@@ -800,7 +818,7 @@ cudaError_t launch_tc_gj(const float2* src, int64_t src_stride, float2* out, int
   int dev = 0, nsm = 0;
   RCI_CUDA_TRY(cudaGetDevice(&dev));
   RCI_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  GjtArgs a{src, src_stride, out, out_stride, n, batch, status, tc_wait_limit(), 0};
+  GjtArgs a{src, src_stride, out, out_stride, n, batch, status, tc_wait_limit(), 0, maxabs};
   a.vec16 = (n % 2 == 0) && ((uintptr_t)src % 16 == 0) && (src_stride % 2 == 0);
   const int grid = batch < nsm ? batch : nsm;
   tc_gj_kernel<<<grid, GJT_THREADS, GJT_SMEM, s>>>(a);

@@ -391,3 +391,19 @@ def test_fp32_grid_falls_back_to_fp64_when_refinement_fails():
         assert not info3.fallback and abs(F3 - F64) <= 1e-8 * F64
     F_ref, _ = Evaluation(wl, ws).reciprocal()
     assert abs(F - F_ref) <= 1e-9 * F_ref
+
+
+def test_growth_estimate_is_reported_and_precision_independent():
+    # the largest entry of the inverted Schur complements over the largest of A: the same
+    # blocks in FP32 and FP64 up to rounding, finite and of order one for these grids
+    wl = W.c1_concentrator()
+    ws = W.widths(wl.grid.n_cells, 4)
+    g_est = {}
+    for prec in (P.FP32_REFINE, P.FP64):
+        with P.Grid(wl.grid, prec=prec) as g:
+            g.set_design(ws)
+            g.factor()
+            _, info = g.avg_intensity(wl.objective, wl.light)
+            g_est[prec] = info.growth_est
+    assert np.isfinite(g_est[P.FP64]) and 1e-2 < g_est[P.FP64] < 1e4, g_est
+    assert abs(g_est[P.FP32_REFINE] - g_est[P.FP64]) <= 1e-4 * g_est[P.FP64], g_est
