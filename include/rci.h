@@ -71,9 +71,10 @@ typedef enum {
 } rci_objective_kind;
 
 typedef enum {
-  RCI_LIGHT_CONE = 0,      /* rho uniform in theta on [-c, c] */
-  RCI_LIGHT_ANNULUS = 1,   /* rho uniform in theta on [th1, th2] U [-th2, -th1] */
-  RCI_LIGHT_USER_LAGS = 2  /* real, even W given as lags W(m h), m = 0..n_src-1 */
+  RCI_LIGHT_CONE = 0,       /* rho uniform in theta on [-c, c] */
+  RCI_LIGHT_ANNULUS = 1,    /* rho uniform in theta on [th1, th2] U [-th2, -th1] */
+  RCI_LIGHT_USER_LAGS = 2,  /* real, even W given as lags W(m h), m = 0..n_src-1 */
+  RCI_LIGHT_TABULATED = 3   /* rho given at angles: piecewise linear in theta, even (below) */
 } rci_light_kind;
 
 /* Problem geometry (lengths in wavelengths, counts in grid cells). */
@@ -111,6 +112,17 @@ typedef struct {
   double c;              /* CONE half-angle (radians, 0 < c < pi/2) */
   double th1, th2;       /* ANNULUS bounds (0 <= th1 < th2 < pi/2) */
   const double* lags;    /* USER_LAGS: HOST float64[n_src] */
+  /* TABULATED: the angular density (Sec. 3's <|a(theta)|^2>) at n_tab angles
+   * 0 <= theta[0] < theta[1] < ... < theta[n_tab-1] < pi/2 (radians, in the substrate),
+   * rho[q] >= 0, linear in theta between nodes, zero outside [theta[0], theta[n_tab-1]] and
+   * even (rho(-theta) = rho(theta)), so that
+   *   W(D) = 2 int rho(theta) cos(theta) cos(k_s sin(theta) D) dtheta,
+   * evaluated on the device by composite Gauss-Legendre quadrature in u = sin(theta) on
+   * sub-panels no wider than half an oscillation period over the source plane.  The values
+   * are used as given (no normalisation).  HOST float64[n_tab] each, 2 <= n_tab <= 65536. */
+  const double* tab_theta;
+  const double* tab_rho;
+  int64_t n_tab;
 } rci_light;
 
 typedef struct {

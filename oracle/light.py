@@ -20,6 +20,13 @@ sin(theta), so
 with sinc(z) = sin(z)/z.  (The printed formulas drop the Jacobian and the index and
 carry theta where sin(theta) is exact; the printed forms are still reachable through
 LIGHT_USER_LAGS.)  W is real and even for these symmetric densities.
+
+A tabulated density (LIGHT_TABULATED) is given at nodes 0 <= theta_0 < ... < theta_{n-1}
+< pi/2, linear in theta between nodes, zero outside, and even (rho(-theta) = rho(theta)), so
+
+    W(Delta) = 2 int_{theta_0}^{theta_{n-1}} rho(theta) cos(theta) cos(k_s sin(theta) Delta) d theta,
+
+integrated here segment by segment with a composite Gauss-Legendre rule in theta.
 """
 from __future__ import annotations
 
@@ -27,7 +34,7 @@ import math
 
 import numpy as np
 
-from workloads import Light, LIGHT_CONE, LIGHT_ANNULUS, LIGHT_USER_LAGS
+from workloads import Light, LIGHT_CONE, LIGHT_ANNULUS, LIGHT_USER_LAGS, LIGHT_TABULATED
 
 
 def gauss_legendre(n: int):
@@ -118,8 +125,42 @@ def W_of_delta(light: Light, k_s: float, delta):
     raise ValueError("closed form only for cone and annulus")
 
 
+def W_tabulated(theta, rho_tab, k_s: float, delta, order: int = 20) -> np.ndarray:
+    """W(Delta) of a tabulated, piecewise-linear, even density (module docstring): on each
+    segment, sub-panels in theta no wider than a third of the shortest oscillation period
+    of cos(k_s sin(theta) Delta) over the requested Delta, `order` Gauss-Legendre points each."""
+    theta = np.asarray(theta, dtype=np.float64)
+    rho_tab = np.asarray(rho_tab, dtype=np.float64)
+    delta = np.atleast_1d(np.asarray(delta, dtype=np.float64))
+    dmax = float(np.max(np.abs(delta))) if delta.size else 0.0
+    x, w = gauss_legendre(order)
+    th_all, c_all = [], []
+    for q in range(theta.size - 1):
+        a, b = theta[q], theta[q + 1]
+        # |d/dtheta (k_s sin(theta) Delta)| <= k_s Delta: period >= 2 pi / (k_s Delta)
+        panels = max(1, int(math.ceil((b - a) * k_s * dmax / (2 * math.pi / 3))))
+        edges = np.linspace(a, b, panels + 1)
+        mid = 0.5 * (edges[1:] + edges[:-1])
+        half = 0.5 * (edges[1:] - edges[:-1])
+        th = (mid[:, None] + half[:, None] * x[None, :]).ravel()
+        wt = (half[:, None] * w[None, :]).ravel()
+        r = rho_tab[q] + (rho_tab[q + 1] - rho_tab[q]) * (th - a) / (b - a)
+        th_all.append(th)
+        c_all.append(2.0 * wt * r * np.cos(th))
+    th = np.concatenate(th_all)
+    cw = np.concatenate(c_all)
+    s = np.sin(th)
+    out = np.empty(delta.shape)
+    for i0 in range(0, delta.size, 512):
+        d = delta[i0:i0 + 512]
+        out[i0:i0 + 512] = np.cos(k_s * np.outer(d, s)) @ cw
+    return out
+
+
 def W_lags(light: Light, k_s: float, h: float, n: int) -> np.ndarray:
     """W(m h) for m = 0..n-1 (the Toeplitz symbol on the source plane)."""
+    if light.kind == LIGHT_TABULATED:
+        return W_tabulated(light.theta, light.rho, k_s, h * np.arange(n))
     if light.kind == LIGHT_USER_LAGS:
         lags = np.asarray(light.lags, dtype=np.float64)
         if lags.shape != (n,):

@@ -1,6 +1,7 @@
 // C ABI of the reciprocal incoherent-light evaluator (declarations and contracts in
 // include/rci.h).  Host code here only validates arguments, sequences kernels on the
 // grid's stream and moves scalars; every numerical step runs in the kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -69,6 +70,9 @@ struct rci_grid {
   // light cache
   bool lags_valid = false;
   rci_light lags_key{};
+  std::vector<double> tab_key;    // TABULATED light of the cached lags: theta then rho
+  void* tabbuf = nullptr;         // device: theta, rho, sub-panel table, rule, nodes
+  size_t tabbuf_bytes = 0;
   // settings
   double tol32 = 1e-10, tol64 = 1e-13;
   int max_refine32 = 31, max_refine64 = 2;  // FP32: solves, the first one included
@@ -183,6 +187,8 @@ bool light_eq(const rci_light& a, const rci_light& b) {
   return a.kind == b.kind && a.c == b.c && a.th1 == b.th1 && a.th2 == b.th2 && a.lags == b.lags;
 }
 
+constexpr int64_t TAB_MAX = 65536;
+
 rci_status check_light(rci_grid* g, const rci_light* L) {
   if (!L) return fail(g, RCI_EINVAL, "light is NULL");
   if (L->kind == RCI_LIGHT_CONE) {
@@ -192,6 +198,16 @@ rci_status check_light(rci_grid* g, const rci_light* L) {
       return fail(g, RCI_EINVAL, "annulus needs 0 <= th1 < th2 < pi/2");
   } else if (L->kind == RCI_LIGHT_USER_LAGS) {
     if (!L->lags) return fail(g, RCI_EINVAL, "user lags pointer is NULL");
+  } else if (L->kind == RCI_LIGHT_TABULATED) {
+    if (!L->tab_theta || !L->tab_rho || L->n_tab < 2 || L->n_tab > TAB_MAX)
+      return fail(g, RCI_EINVAL, "tabulated light needs 2 <= n_tab <= 65536 angles and densities");
+    for (int64_t q = 0; q < L->n_tab; ++q) {
+      const double t = L->tab_theta[q], r = L->tab_rho[q];
+      if (!(t >= 0.0 && t < M_PI / 2) || (q > 0 && !(t > L->tab_theta[q - 1])))
+        return fail(g, RCI_EINVAL, "tabulated angles must ascend strictly within [0, pi/2)");
+      if (!(r >= 0.0) || !std::isfinite(r))
+        return fail(g, RCI_EINVAL, "tabulated densities must be finite and >= 0");
+    }
   } else {
     return fail(g, RCI_EINVAL, "unknown light kind");
   }
@@ -205,6 +221,58 @@ rci_status ensure_lags(rci_grid* g, const rci_light* L) {
     CK(cudaMemcpyAsync(g->lags, L->lags, sizeof(double) * g->g.n_src, cudaMemcpyHostToDevice, g->s),
        "copy lags");
     g->lags_valid = false;
+    return RCI_OK;
+  }
+  if (L->kind == RCI_LIGHT_TABULATED) {
+    const int64_t nt = L->n_tab;
+    std::vector<double> key(L->tab_theta, L->tab_theta + nt);
+    key.insert(key.end(), L->tab_rho, L->tab_rho + nt);
+    if (g->lags_valid && g->lags_key.kind == RCI_LIGHT_TABULATED && g->tab_key == key)
+      return RCI_OK;
+    // sub-panels: each segment split into equal parts in u = sin(theta) no wider than half
+    // the shortest period of cos(k_s u D) over the source plane (D <= (n_src - 1) h)
+    const double dmax = (double)(g->g.n_src - 1) * g->g.h;
+    const double umax = M_PI / (g->g.k_sub * (dmax > 0.0 ? dmax : g->g.h));
+    std::vector<int4> seg;
+    for (int64_t q = 0; q + 1 < nt; ++q) {
+      const double du = std::sin(L->tab_theta[q + 1]) - std::sin(L->tab_theta[q]);
+      const int S = (int)std::max(1.0, std::ceil(du / umax));
+      for (int i = 0; i < S; ++i) seg.push_back(make_int4((int)q, i, S, 0));
+    }
+    const int P = (int)seg.size();
+    if ((int64_t)P * TAB_ORDER > (1 << 26)) return fail(g, RCI_EINVAL, "tabulated light too fine");
+    const size_t need = sizeof(double) * 2 * nt + sizeof(int4) * P + sizeof(double) * 2 * TAB_ORDER +
+                        sizeof(double2) * (size_t)P * TAB_ORDER + 64 * 5;
+    if (g->tabbuf_bytes < need) {
+      dfree(g, g->tabbuf);
+      g->tabbuf = nullptr;
+      g->tabbuf_bytes = 0;
+      CK(dalloc(g, (char**)&g->tabbuf, need), "tabulated light");
+      g->tabbuf_bytes = need;
+    }
+    auto carve = [](char*& p, size_t b) { char* r = p; p += (b + 63) & ~(size_t)63; return r; };
+    char* p = (char*)g->tabbuf;
+    double* th_d = (double*)carve(p, sizeof(double) * nt);
+    double* rho_d = (double*)carve(p, sizeof(double) * nt);
+    int4* seg_d = (int4*)carve(p, sizeof(int4) * P);
+    double* glx = (double*)carve(p, sizeof(double) * TAB_ORDER);
+    double* glw = (double*)carve(p, sizeof(double) * TAB_ORDER);
+    double2* node = (double2*)carve(p, sizeof(double2) * (size_t)P * TAB_ORDER);
+    g->tab_key = std::move(key);
+    CK(cudaMemcpyAsync(th_d, g->tab_key.data(), sizeof(double) * nt, cudaMemcpyHostToDevice, g->s),
+       "tabulated light");
+    CK(cudaMemcpyAsync(rho_d, g->tab_key.data() + nt, sizeof(double) * nt, cudaMemcpyHostToDevice,
+                       g->s),
+       "tabulated light");
+    CK(cudaMemcpyAsync(seg_d, seg.data(), sizeof(int4) * P, cudaMemcpyHostToDevice, g->s),
+       "tabulated light");
+    CK(launch_w_lags_tabulated(th_d, rho_d, seg_d, P, glx, glw, node, g->g.k_sub, g->g.h,
+                               g->g.n_src, g->lags, g->s),
+       "W lags (tabulated)");
+    // the sub-panel table is a local vector: its copy must be done before it goes away
+    CK(cudaStreamSynchronize(g->s), "tabulated light");
+    g->lags_key = *L;
+    g->lags_valid = true;
     return RCI_OK;
   }
   if (g->lags_valid && light_eq(g->lags_key, *L)) return RCI_OK;
@@ -542,7 +610,8 @@ void destroy_grid(rci_grid* g, bool sync) {
   void* ps[] = {g->widths, g->eps, g->dg, g->cx, g->cy, g->dg0, g->kss, g->b1, g->x1, g->r1, g->r32, g->d32,
                 g->crow, g->vsrc, g->lags, g->qpart, g->dscal, g->part_r, g->part_b, g->ratio,
                 g->vf_scratch, g->dstatus, g->mb, g->mx, g->mr, g->m32a, g->m32b, g->th_d,
-                g->wq_d, g->f_d, g->mu, g->gsrc, g->tpart, g->dgrad, g->cbuf, g->mF};
+                g->wq_d, g->f_d, g->mu, g->gsrc, g->tpart, g->dgrad, g->cbuf, g->mF,
+                g->tabbuf};
   for (void* p : ps) dfree(g, p);
   g->mem64.release(g->corr64);
   bcr_destroy(g->bcr);

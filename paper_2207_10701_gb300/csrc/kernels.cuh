@@ -65,6 +65,12 @@ cudaError_t launch_conj(double2* a, int64_t n, cudaStream_t s);
 cudaError_t launch_light_rule(int kind, double c, double th1, double th2, int nq, double* theta,
                               double* wrho, cudaStream_t s);
 // W lags (closed forms) m = 0..n-1
+// tabulated density: the composite rule's nodes (P sub-panels of TAB_ORDER points) and the
+// lags; glx, glw: TAB_ORDER doubles each, node: P * TAB_ORDER entries (device scratch)
+constexpr int TAB_ORDER = 12;
+cudaError_t launch_w_lags_tabulated(const double* theta, const double* rho, const int4* seg, int P,
+                                   double* glx, double* glw, double2* node, double k_s, double h,
+                                   int64_t n, double* lags, cudaStream_t s);
 cudaError_t launch_w_lags(int kind, double c, double th1, double th2, double k_s, double h,
                           int64_t n, double* lags, cudaStream_t s);
 // weighted sum out = sum_q w_q f_q (single block, deterministic)

@@ -84,6 +84,47 @@ __global__ void w_lags_kernel(int kind, double c, double th1, double th2, double
   lags[m] = v;
 }
 
+// Tabulated density (rci_light TABULATED): nodes of the composite rule in u = sin(theta).
+// Sub-panel p lies in segment seg[p].x (between theta[q] and theta[q+1]), and is sub-panel
+// seg[p].y of seg[p].z equal parts of that segment in u; TAB_ORDER Gauss-Legendre points each.
+//   node[j] = (u_j, 2 w_j rho(asin u_j)),  since cos(theta) d theta = du
+__global__ void tab_nodes_kernel(const double* __restrict__ theta, const double* __restrict__ rho,
+                                 const int4* __restrict__ seg, int P, const double* __restrict__ gx,
+                                 const double* __restrict__ gw, double2* __restrict__ node) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= P * TAB_ORDER) return;
+  const int p = j / TAB_ORDER, o = j - p * TAB_ORDER;
+  const int4 sg = seg[p];
+  const int q = sg.x;
+  const double ua = sin(theta[q]), ub = sin(theta[q + 1]);
+  const double a = ua + (ub - ua) * (double)sg.y / (double)sg.z;
+  const double b = ua + (ub - ua) * (double)(sg.y + 1) / (double)sg.z;
+  const double half = 0.5 * (b - a), mid = 0.5 * (a + b);
+  const double u = mid + half * gx[o];
+  const double th = asin(u);
+  const double r = rho[q] + (rho[q + 1] - rho[q]) * (th - theta[q]) / (theta[q + 1] - theta[q]);
+  node[j] = make_double2(u, 2.0 * half * gw[o] * r);
+}
+
+// lags[m] = sum_j c_j cos(k_s u_j m h), nodes staged through shared memory
+constexpr int TAB_TILE = 256;
+__global__ void __launch_bounds__(TAB_TILE)
+tab_lags_kernel(const double2* __restrict__ node, int J, double k_s, double h, int64_t n,
+                double* __restrict__ lags) {
+  __shared__ double2 sn[TAB_TILE];
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const double kd = k_s * h * (double)m;
+  double acc = 0.0;
+  for (int j0 = 0; j0 < J; j0 += TAB_TILE) {
+    if (j0 + (int)threadIdx.x < J) sn[threadIdx.x] = node[j0 + threadIdx.x];
+    __syncthreads();
+    const int jn = J - j0 < TAB_TILE ? J - j0 : TAB_TILE;
+    for (int j = 0; j < jn; ++j) acc = fma(sn[j].y, cos(kd * sn[j].x), acc);
+    __syncthreads();
+  }
+  if (m < n) lags[m] = acc;
+}
+
 // ----------------------------------------------------------------- objectives / sources
 __global__ void planewave_row_kernel(GridGeom g, double theta_out, double2* __restrict__ crow) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -274,6 +315,20 @@ cudaError_t launch_light_rule(int kind, double c, double th1, double th2, int nq
 cudaError_t launch_w_lags(int kind, double c, double th1, double th2, double k_s, double h,
                           int64_t n, double* lags, cudaStream_t s) {
   w_lags_kernel<<<(unsigned)ceil_div(n, 256), 256, 0, s>>>(kind, c, th1, th2, k_s, h, n, lags); rci_note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_w_lags_tabulated(const double* theta, const double* rho, const int4* seg, int P,
+                                   double* glx, double* glw, double2* node, double k_s, double h,
+                                   int64_t n, double* lags, cudaStream_t s) {
+  if (P < 1) return cudaErrorInvalidValue;
+  RCI_CUDA_TRY(launch_gauss_legendre(TAB_ORDER, -1.0, 1.0, glx, glw, s));
+  const int J = P * TAB_ORDER;
+  tab_nodes_kernel<<<(unsigned)ceil_div(J, 128), 128, 0, s>>>(theta, rho, seg, P, glx, glw, node);
+  rci_note_launch();
+  RCI_CUDA_TRY(cudaGetLastError());
+  tab_lags_kernel<<<(unsigned)ceil_div(n, TAB_TILE), TAB_TILE, 0, s>>>(node, J, k_s, h, n, lags);
+  rci_note_launch();
   return cudaGetLastError();
 }
 

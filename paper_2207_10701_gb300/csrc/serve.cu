@@ -47,6 +47,7 @@ struct Request {
   std::vector<double> w_row;   // USER_ROW objective (copied)
   rci_light light{};
   std::vector<double> lags;    // USER_LAGS light (copied)
+  std::vector<double> tab;     // TABULATED light: angles then densities (copied)
   int want_grad = 0;
   uint64_t key = 0;
   double* grad_out = nullptr;
@@ -361,6 +362,14 @@ rci_status copy_request(rci_server* s, const rci_request* q, Request* r) {
     if (!q->light.lags) return RCI_EINVAL;
     r->lags.assign(q->light.lags, q->light.lags + n_src);
     r->light.lags = r->lags.data();
+  }
+  if (q->light.kind == RCI_LIGHT_TABULATED) {
+    const int64_t nt = q->light.n_tab;
+    if (!q->light.tab_theta || !q->light.tab_rho || nt < 2 || nt > 65536) return RCI_EINVAL;
+    r->tab.assign(q->light.tab_theta, q->light.tab_theta + nt);
+    r->tab.insert(r->tab.end(), q->light.tab_rho, q->light.tab_rho + nt);
+    r->light.tab_theta = r->tab.data();
+    r->light.tab_rho = r->tab.data() + nt;
   }
   r->want_grad = q->want_grad != 0;
   if (r->want_grad && !q->grad_out) return RCI_EINVAL;

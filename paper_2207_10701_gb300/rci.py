@@ -11,7 +11,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librci.so")
 
 OBJ_POINT, OBJ_PLANEWAVE, OBJ_VIRTUAL_FOCUS, OBJ_USER_ROW = 0, 1, 2, 3
-LIGHT_CONE, LIGHT_ANNULUS, LIGHT_USER_LAGS = 0, 1, 2
+LIGHT_CONE, LIGHT_ANNULUS, LIGHT_USER_LAGS, LIGHT_TABULATED = 0, 1, 2, 3
 FP64, FP32_REFINE = 0, 1
 
 STATUS = {0: "RCI_OK", 1: "RCI_EINVAL", 2: "RCI_ENOMEM", 3: "RCI_ECUDA", 4: "RCI_ESTATE",
@@ -36,7 +36,9 @@ class ObjectiveC(C.Structure):
 
 class LightC(C.Structure):
     _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("c", C.c_double),
-                ("th1", C.c_double), ("th2", C.c_double), ("lags", C.POINTER(C.c_double))]
+                ("th1", C.c_double), ("th2", C.c_double), ("lags", C.POINTER(C.c_double)),
+                ("tab_theta", C.POINTER(C.c_double)), ("tab_rho", C.POINTER(C.c_double)),
+                ("n_tab", C.c_int64)]
 
 
 class InfoC(C.Structure):
@@ -221,11 +223,19 @@ def _objective(o, keep):
 
 
 def _light(L, keep):
-    lags = None
+    lags = th = rh = None
     if L.kind == LIGHT_USER_LAGS:
         lags = np.ascontiguousarray(np.asarray(L.lags, dtype=np.float64))
         keep.append(lags)
-    return LightC(L.kind, 0, L.c, L.th1, L.th2, _hptr(lags) if lags is not None else None)
+    if L.kind == LIGHT_TABULATED:
+        th = np.ascontiguousarray(np.asarray(L.theta, dtype=np.float64))
+        rh = np.ascontiguousarray(np.asarray(L.rho, dtype=np.float64))
+        if th.shape != rh.shape or th.ndim != 1:
+            raise ValueError("tabulated light: theta and rho of equal length")
+        keep.extend((th, rh))
+    return LightC(L.kind, 0, L.c, L.th1, L.th2, _hptr(lags) if lags is not None else None,
+                  _hptr(th) if th is not None else None, _hptr(rh) if rh is not None else None,
+                  th.size if th is not None else 0)
 
 
 class Grid:

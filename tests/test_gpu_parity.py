@@ -407,3 +407,44 @@ def test_growth_estimate_is_reported_and_precision_independent():
             g_est[prec] = info.growth_est
     assert np.isfinite(g_est[P.FP64]) and 1e-2 < g_est[P.FP64] < 1e4, g_est
     assert abs(g_est[P.FP32_REFINE] - g_est[P.FP64]) <= 1e-4 * g_est[P.FP64], g_est
+
+
+def _tab_light(kind):
+    if kind == "cone":
+        c = math.radians(20)
+        return W.Light(W.LIGHT_TABULATED, theta=np.array([0.0, c]), rho=np.full(2, 1 / (2 * c)))
+    th = np.linspace(0.0, math.radians(35), 23)
+    th[1:-1] += np.random.default_rng(5).uniform(-0.003, 0.003, 21)
+    return W.Light(W.LIGHT_TABULATED, theta=th, rho=np.cos(2.2 * th) ** 2 + 0.1 * th)
+
+
+@pytest.mark.parametrize("prec", [P.FP64, P.FP32_REFINE])
+def test_tabulated_light_matches_oracle(prec):
+    wl = CASES["small_plane"]()
+    g, ws = _grid(wl, prec, seed=3)
+    g.factor()
+    for kind in ("cone", "curved"):
+        light = _tab_light(kind)
+        wl2 = W.Workload("t", wl.grid, wl.objective, light, 0)
+        F_ref, _ = Evaluation(wl2, ws).reciprocal()
+        F, _ = g.avg_intensity(wl.objective, light)
+        assert abs(F - F_ref) <= TOL_F[prec] * F_ref, (kind, F, F_ref)
+    # a tabulated constant density on [0, c] is the cone
+    Fc, _ = g.avg_intensity(wl.objective, W.Light(W.LIGHT_CONE, c=math.radians(20)))
+    Ft, _ = g.avg_intensity(wl.objective, _tab_light("cone"))
+    assert abs(Ft - Fc) <= 1e-11 * Fc
+    g.close()
+
+
+def test_tabulated_light_full_size_against_oracle():
+    # the 200-wavelength grid: lags out to 200 wavelengths (the quadrature's sub-panels follow
+    # the oscillation of cos(k_s sin(theta) D))
+    wl = W.c2_collimator()
+    g, ws = _grid(wl, P.FP32_REFINE, seed=2)
+    g.factor()
+    light = _tab_light("curved")
+    wl2 = W.Workload("t", wl.grid, wl.objective, light, 0)
+    F_ref, _ = Evaluation(wl2, ws).reciprocal()
+    F, _ = g.avg_intensity(wl.objective, light)
+    g.close()
+    assert abs(F - F_ref) <= 1e-8 * F_ref, (F, F_ref)

@@ -94,3 +94,52 @@ def test_W_lags_user_passthrough_and_shape():
     c = W.Light(W.LIGHT_CONE, c=0.3)
     assert np.allclose(W_lags(c, 3.0, 0.05, 5), W_of_delta(c, 3.0, 0.05 * np.arange(5)))
     assert rho(c, 0.1) == pytest.approx(1 / 0.6) and rho(c, 0.31) == 0.0
+
+
+# ---- tabulated densities (piecewise linear in theta, even)
+def _tab_W(theta, rho_tab, k_s, delta):
+    from oracle.light import W_tabulated
+    return W_tabulated(theta, rho_tab, k_s, delta)
+
+
+def test_tabulated_constant_density_reproduces_the_cone_and_annulus_closed_forms():
+    import workloads as W
+    from oracle.light import W_of_delta
+    k_s = 2 * math.pi * math.sqrt(2.1)
+    delta = 0.05 * np.arange(0, 4000, 7)
+    c = math.radians(20)
+    got = _tab_W([0.0, c], [1 / (2 * c)] * 2, k_s, delta)
+    want = W_of_delta(W.Light(W.LIGHT_CONE, c=c), k_s, delta)
+    assert np.max(np.abs(got - want)) < 1e-12 * np.max(np.abs(want))
+    t1, t2 = math.radians(10), math.radians(30)
+    got = _tab_W([t1, t2], [1 / (2 * (t2 - t1))] * 2, k_s, delta)
+    want = W_of_delta(W.Light(W.LIGHT_ANNULUS, th1=t1, th2=t2), k_s, delta)
+    assert np.max(np.abs(got - want)) < 1e-12 * np.max(np.abs(want))
+
+
+def test_tabulated_density_against_adaptive_quadrature():
+    # a curved profile sampled at uneven nodes: the composite rule against scipy's adaptive
+    # quadrature of the same piecewise-linear density, segment by segment
+    import scipy.integrate as si
+    k_s = 2 * math.pi * math.sqrt(2.1)
+    theta = np.sort(np.concatenate([[0.0], np.random.default_rng(7).uniform(0.02, 0.6, 11), [0.62]]))
+    rho_tab = np.cos(2.5 * theta) ** 2
+    for d in (0.0, 0.37, 3.05, 41.2):
+        got = _tab_W(theta, rho_tab, k_s, [d])[0]
+        ref = 0.0
+        for q in range(theta.size - 1):
+            a, b = theta[q], theta[q + 1]
+            f = lambda t: 2 * (rho_tab[q] + (rho_tab[q + 1] - rho_tab[q]) * (t - a) / (b - a)) \
+                * math.cos(t) * math.cos(k_s * math.sin(t) * d)
+            ref += si.quad(f, a, b, epsabs=1e-15, epsrel=1e-14, limit=500)[0]
+        assert abs(got - ref) < 1e-12 * max(1.0, abs(ref)), (d, got, ref)
+
+
+def test_tabulated_density_vanishing_width_limit():
+    # a narrow triangle of unit area around theta0: W -> 2 cos(theta0) cos(k_s sin(theta0) D),
+    # to second order in the width (about e^2 (k_s D)^2 / 12)
+    k_s = 2 * math.pi * math.sqrt(2.1)
+    t0, e = 0.3, 1e-6
+    got = _tab_W([t0 - e, t0, t0 + e], [0.0, 1 / e, 0.0], k_s, [0.0, 1.3, 7.9])
+    want = 2 * math.cos(t0) * np.cos(k_s * math.sin(t0) * np.array([0.0, 1.3, 7.9]))
+    assert np.max(np.abs(got - want)) < 1e-8

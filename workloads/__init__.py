@@ -41,6 +41,7 @@ OBJ_USER_ROW = 3       # caller-supplied w on the monitor row
 LIGHT_CONE = 0         # uniform in theta on [-c, c]
 LIGHT_ANNULUS = 1      # uniform in theta on [th1, th2] U [-th2, -th1]
 LIGHT_USER_LAGS = 2    # caller-supplied real, even W(m h), m = 0..n_src-1
+LIGHT_TABULATED = 3    # rho given at angles 0 <= theta_0 < ... < pi/2, piecewise linear, even
 
 PREC_FP64 = 0
 PREC_FP32_REFINE = 1
@@ -84,6 +85,8 @@ class Light:
     th1: float = 0.0
     th2: float = 0.0
     lags: np.ndarray | None = None    # LIGHT_USER_LAGS: float64[n_src]
+    theta: np.ndarray | None = None   # LIGHT_TABULATED: nodes (radians, ascending, in [0, pi/2))
+    rho: np.ndarray | None = None     # LIGHT_TABULATED: density at the nodes (>= 0)
 
 
 @dataclasses.dataclass
