@@ -162,14 +162,21 @@ __device__ __forceinline__ void tri_forward_unit(const TriRow<T>& f, int n, int 
 // Thread b forms column b of T^{-1} by a tridiagonal solve with the unit vector e_b; the
 // forward sweep goes to a separate scratch column so the backward sweep's loads do not
 // wait on its own stores.
+// Dense Schur blocks of the first reduced system, one block per kept row e = 2k:
+//   D'_k = T_e - diag(cx[e-1]) T_{e-1}^{-1} diag(cx[e-1]) - diag(cx[e]) T_{e+1}^{-1} diag(cx[e])
+//   L'_k = -diag(cx[e-1]) T_{e-1}^{-1} diag(cx[e-2])
+// Thread b forms column b of both inverses: the forward sweeps of the unit vector e_b go to
+// two scratch columns (YR, YL: the next level's free working arrays), then one backward
+// sweep runs both recurrences side by side, so that every entry of D'_k is formed in one
+// step (no read-back of a partial D'), with the scratch loads issued a few rows ahead.
 template <typename T>
 __global__ void level0_schur_kernel(const double2* __restrict__ dg, const double2* __restrict__ cx,
                                     const double2* __restrict__ cy, int nx, int ny, int m0,
                                     const cplx<T>* __restrict__ tdl, const cplx<T>* __restrict__ tdinv,
                                     const cplx<T>* __restrict__ tdu, const cplx<T>* __restrict__ tdu2,
                                     const uint8_t* __restrict__ tpiv, cplx<T>* __restrict__ Dn,
-                                    cplx<T>* __restrict__ Ln, cplx<T>* __restrict__ scratch,
-                                    cplx<T>* __restrict__ G0) {
+                                    cplx<T>* __restrict__ Ln, cplx<T>* __restrict__ scrR,
+                                    cplx<T>* __restrict__ scrL, cplx<T>* __restrict__ G0) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   cplx<T>* sm = reinterpret_cast<cplx<T>*>(sm_raw);
   // [0,4ny): right factors, [4ny,8ny): left factors, then cxl2, cxl, cxr, dge, cye; piv bytes last
@@ -196,6 +203,8 @@ __global__ void level0_schur_kernel(const double2* __restrict__ dg, const double
       R[3 * ny + j] = tdu2[b];
       pivR[j] = tpiv[b];
       cxr[j] = ccast<T>(cx[e * ny + j]);
+    } else {
+      cxr[j] = czero<T>();
     }
     if (has_l) {
       int64_t b = (int64_t)(k - 1) * ny + j;
@@ -206,6 +215,8 @@ __global__ void level0_schur_kernel(const double2* __restrict__ dg, const double
       pivL[j] = tpiv[b];
       cxl[j] = ccast<T>(cx[(e - 1) * ny + j]);
       cxl2[j] = ccast<T>(cx[(e - 2) * ny + j]);
+    } else {
+      cxl[j] = cxl2[j] = czero<T>();
     }
     dge[j] = ccast<T>(dg[e * ny + j]);
     cye[j] = ccast<T>(cy[e * ny + j]);
@@ -216,36 +227,48 @@ __global__ void level0_schur_kernel(const double2* __restrict__ dg, const double
   const int64_t nn = (int64_t)ny * ny;
   cplx<T>* __restrict__ Dcol = Dn + (int64_t)k * nn + b;
   cplx<T>* __restrict__ Lcol = Ln + (int64_t)k * nn + b;
-  cplx<T>* __restrict__ Ycol = scratch + (int64_t)k * nn + b;
+  cplx<T>* __restrict__ YR = scrR + (int64_t)k * nn + b;
+  cplx<T>* __restrict__ YL = scrL + (int64_t)k * nn + b;
   cplx<T>* __restrict__ Gcol = G0 + (int64_t)k * nn + b;
-  auto Te = [&](int a) -> cplx<T> {
-    if (a == b) return dge[a];
-    if (a == b - 1) return cye[a];
-    if (a == b + 1) return cye[b];
-    return czero<T>();
-  };
-  if (has_r) {
-    TriRow<T> f{R, R + ny, R + 2 * ny, R + 3 * ny, pivR};
-    tri_forward_unit<T>(f, ny, b, Ycol, ny);
-    const cplx<T> sb = cxr[b];
-    tri_backward<T>(f, ny, [&](int a) { return Ycol[(int64_t)a * ny]; },
-                    [&](int a, cplx<T> g) {
-                      Dcol[(int64_t)a * ny] = cfms(cxr[a] * g, sb, Te(a));
-                      Gcol[(int64_t)a * ny] = g;  // T_{e+1}^{-1}, kept for the solve
-                    });
-  } else {
-    for (int a = 0; a < ny; ++a) Dcol[(int64_t)a * ny] = Te(a);
+  const TriRow<T> fR{R, R + ny, R + 2 * ny, R + 3 * ny, pivR};
+  const TriRow<T> fL{Lf, Lf + ny, Lf + 2 * ny, Lf + 3 * ny, pivL};
+  if (has_r) tri_forward_unit<T>(fR, ny, b, YR, ny);
+  if (has_l) tri_forward_unit<T>(fL, ny, b, YL, ny);
+  const cplx<T> sb = cxr[b], sl = cxl[b], sl2 = cxl2[b];
+  cplx<T> r1 = czero<T>(), r2 = czero<T>(), l1 = czero<T>(), l2 = czero<T>();
+  // scratch values of the next PF rows, loaded ahead of the recurrences
+  constexpr int PF = 4;
+  cplx<T> yr[PF], yl[PF];
+#pragma unroll
+  for (int q = 0; q < PF; ++q) {
+    const int a = ny - 1 - q;
+    yr[q] = (has_r && a >= 0) ? YR[(int64_t)a * ny] : czero<T>();
+    yl[q] = (has_l && a >= 0) ? YL[(int64_t)a * ny] : czero<T>();
   }
-  if (has_l) {
-    TriRow<T> f{Lf, Lf + ny, Lf + 2 * ny, Lf + 3 * ny, pivL};
-    tri_forward_unit<T>(f, ny, b, Ycol, ny);
-    const cplx<T> sl = cxl[b], sl2 = cxl2[b];
-    tri_backward<T>(f, ny, [&](int a) { return Ycol[(int64_t)a * ny]; },
-                    [&](int a, cplx<T> g) {
-                      cplx<T> cg = cxl[a] * g;
-                      Lcol[(int64_t)a * ny] = -(cg * sl2);
-                      Dcol[(int64_t)a * ny] = cfms(cg, sl, Dcol[(int64_t)a * ny]);
-                    });
+  for (int a0 = ny - 1; a0 >= 0; a0 -= PF) {
+#pragma unroll
+    for (int q = 0; q < PF; ++q) {
+      const int a = a0 - q;
+      if (a < 0) break;
+      const cplx<T> cr = yr[q], cl = yl[q];
+      const int an = a - PF;  // the row PF steps ahead into the same ring slot
+      yr[q] = (has_r && an >= 0) ? YR[(int64_t)an * ny] : czero<T>();
+      yl[q] = (has_l && an >= 0) ? YL[(int64_t)an * ny] : czero<T>();
+      // T_{e+1}^{-1} and T_{e-1}^{-1}, entry (a, b)
+      cplx<T> gr = cfms(fR.du2[a], r2, cfms(fR.du[a], r1, cr)) * fR.dinv[a];
+      cplx<T> gl = cfms(fL.du2[a], l2, cfms(fL.du[a], l1, cl)) * fL.dinv[a];
+      if (!has_r) gr = czero<T>();
+      if (!has_l) gl = czero<T>();
+      r2 = r1;
+      r1 = gr;
+      l2 = l1;
+      l1 = gl;
+      const cplx<T> te = a == b ? dge[a] : (a == b - 1 ? cye[a] : (a == b + 1 ? cye[b] : czero<T>()));
+      const cplx<T> cgl = cxl[a] * gl;
+      Dcol[(int64_t)a * ny] = cfms(cgl, sl, cfms(cxr[a] * gr, sb, te));
+      if (has_r) Gcol[(int64_t)a * ny] = gr;  // T_{e+1}^{-1}, kept for the solve
+      if (has_l) Lcol[(int64_t)a * ny] = -(cgl * sl2);
+    }
   }
 }
 
@@ -1965,10 +1988,11 @@ static cudaError_t factor_t(BcrHandle* h, const double2* dg, const double2* cx, 
     if (smem > 48 * 1024)
       RCI_CUDA_TRY(cudaFuncSetAttribute(level0_schur_kernel<T>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    // the next level's working D array is free during level 0 and serves as scratch
+    // the next level's working arrays are free during level 0 and serve as scratch
     level0_schur_kernel<T><<<n1, thr, smem, s>>>(dg, cx, cy, nx, ny, m0, tdl, tdinv, tdu, tdu2,
                                                  h->tpiv, (cplx<T>*)h->Dw[0], (cplx<T>*)h->Lw[0],
-                                                 (cplx<T>*)h->Dw[1], (cplx<T>*)h->G0);
+                                                 (cplx<T>*)h->Dw[1], (cplx<T>*)h->Lw[1],
+                                                 (cplx<T>*)h->G0);
     rci_note_launch();
     RCI_CUDA_TRY(cudaGetLastError());
   }
