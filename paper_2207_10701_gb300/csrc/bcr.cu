@@ -1828,6 +1828,67 @@ bwd0_chunk_kernel(const cplx<T>* __restrict__ G0, const cplx<T>* __restrict__ b,
   if (has) rows_mv<T, SMAX>(G0 + k * (int64_t)ny * ny, rhs, ny, c0, x + r * ny, nullptr);
 }
 
+// ----- single right-hand side, level 0 by the pivoted tridiagonal factors (5 ny values per
+// eliminated row instead of the dense ny x ny inverse): one warp per eliminated row k stages
+// the row's factors and right-hand side in shared memory, lane 0 runs the forward and
+// backward sweeps, the warp writes the result.
+//   FWD: t0[k] = T_{2k+1}^{-1} b[2k+1]
+//   BWD: x[2k] = x1[k];  x[2k+1] = T_{2k+1}^{-1} (b[2k+1] - cx[2k] o x1[k] - cx[2k+1] o x1[k+1])
+constexpr int TRS_WARPS = 4;
+
+template <typename T>
+__host__ __device__ size_t trs_smem_per_warp(int ny) {
+  return ((size_t)5 * ny * sizeof(cplx<T>) + (size_t)ny + 15) & ~(size_t)15;
+}
+
+template <typename T, bool BWD>
+__global__ void __launch_bounds__(32 * TRS_WARPS)
+tri_rows_solve_kernel(const cplx<T>* __restrict__ tdl, const cplx<T>* __restrict__ tdinv,
+                      const cplx<T>* __restrict__ tdu, const cplx<T>* __restrict__ tdu2,
+                      const uint8_t* __restrict__ tpiv, const cplx<T>* __restrict__ b,
+                      const cplx<T>* __restrict__ x1, const double2* __restrict__ cx,
+                      cplx<T>* __restrict__ out, int nx, int ny, int rows) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * TRS_WARPS + w;
+  if (k >= rows) return;  // whole warp
+  cplx<T>* dl = reinterpret_cast<cplx<T>*>(sm_raw + (size_t)w * trs_smem_per_warp<T>(ny));
+  cplx<T>* di = dl + ny;
+  cplx<T>* du = di + ny;
+  cplx<T>* du2 = du + ny;
+  cplx<T>* v = du2 + ny;
+  uint8_t* pv = reinterpret_cast<uint8_t*>(v + ny);
+  const int64_t r = 2 * (int64_t)k + 1;
+  const bool has = r < nx;
+  if (BWD) {
+    for (int j = lane; j < ny; j += 32) out[2 * (int64_t)k * ny + j] = x1[(int64_t)k * ny + j];
+  }
+  if (!has) return;
+  const int64_t fb = (int64_t)k * ny;
+  for (int j = lane; j < ny; j += 32) {
+    dl[j] = tdl[fb + j];
+    di[j] = tdinv[fb + j];
+    du[j] = tdu[fb + j];
+    du2[j] = tdu2[fb + j];
+    pv[j] = tpiv[fb + j];
+    cplx<T> rv = b[r * ny + j];
+    if (BWD) {
+      rv = cfms(ccast<T>(cx[(r - 1) * ny + j]), x1[(int64_t)k * ny + j], rv);
+      if (r + 1 < nx) rv = cfms(ccast<T>(cx[r * ny + j]), x1[(int64_t)(k + 1) * ny + j], rv);
+    }
+    v[j] = rv;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    TriRow<T> f{dl, di, du, du2, pv};
+    tri_forward<T>(f, ny, [&](int j) { return v[j]; }, [&](int j, cplx<T> y) { v[j] = y; });
+    tri_backward<T>(f, ny, [&](int j) { return v[j]; }, [&](int j, cplx<T> g) { v[j] = g; });
+  }
+  __syncwarp();
+  cplx<T>* o = BWD ? out + r * ny : out + (int64_t)k * ny;
+  for (int j = lane; j < ny; j += 32) o[j] = v[j];
+}
+
 }  // namespace
 
 // ===================================================================== handle
@@ -2100,7 +2161,10 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
   const cplx<T>* G0 = (const cplx<T>*)h->G0;
   const cplx<T> one = mkc(T(1), T(0)), mone = mkc(T(-1), T(0)), zero = czero<T>();
 
-  double sbytes = 2.0 * m0 * (double)nn * sizeof(cplx<T>), sflops = 2.0 * 8.0 * m0 * (double)nn * nrhs;
+  // level 0: the tridiagonal factors twice for one right-hand side (dense inverses G0 for
+  // several); levels >= 1: Dinv, X, Y forward and X, Y backward
+  double sbytes = nrhs == 1 ? 2.0 * m0 * 5.0 * ny * sizeof(cplx<T>) : 2.0 * m0 * (double)nn * sizeof(cplx<T>);
+  double sflops = nrhs == 1 ? 2.0 * 30.0 * m0 * (double)ny : 2.0 * 8.0 * m0 * (double)nn * nrhs;
   for (int l = 1; l < h->Lf; ++l) {
     sbytes += 5.0 * h->m[l] * (double)nn * sizeof(cplx<T>);
     sflops += 5.0 * 8.0 * h->m[l] * (double)nn * nrhs;
@@ -2139,10 +2203,23 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
     // the chunked level-0 backward pass reads b while other blocks write x: no aliasing
     const cplx<T>* bsrc = b;
     if ((const void*)b == (const void*)x) return cudaErrorInvalidValue;
-    // ---- level 0 forward: t0[k] = T_{2k+1}^{-1} b[2k+1]
-    if (m0 > 0)
-      RCI_SMAX_DISPATCH(mv_chunk_kernel, dim3(m0, nch), ny * sizeof(cplx<T>), G0, bsrc,
-                        2 * (int64_t)ny, (int64_t)ny, t0, ny);
+    // ---- level 0 forward: t0[k] = T_{2k+1}^{-1} b[2k+1] by tridiagonal sweeps
+    const size_t trs_smem = TRS_WARPS * trs_smem_per_warp<T>(ny);
+    auto trs_attr = [&](auto kern) -> cudaError_t {
+      return trs_smem > 48 * 1024 ? cudaFuncSetAttribute(kern,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         (int)trs_smem)
+                                  : cudaSuccess;
+    };
+    if (m0 > 0) {
+      RCI_CUDA_TRY(trs_attr(tri_rows_solve_kernel<T, false>));
+      tri_rows_solve_kernel<T, false><<<(unsigned)ceil_div(m0, TRS_WARPS), 32 * TRS_WARPS,
+                                        trs_smem, s>>>(
+          (const cplx<T>*)h->tdl, (const cplx<T>*)h->tdinv, (const cplx<T>*)h->tdu,
+          (const cplx<T>*)h->tdu2, h->tpiv, bsrc, nullptr, cx, t0, nx, ny, m0);
+      rci_note_launch();
+      RCI_CUDA_TRY(cudaGetLastError());
+    }
     {
       int64_t nt = (int64_t)n1 * row;
       keep0_kernel<T><<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(bsrc, t0, cx, B[1], nx, ny, n1, 1);
@@ -2175,9 +2252,14 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
       RCI_SMAX_DISPATCH(bwd_chunk_kernel, dim3(nk, nch), 3 * ny * sizeof(cplx<T>), X, Y, tl[l],
                         B[l + 1], B[l], n, m, ny);
     }
-    // ---- level 0 backward
-    RCI_SMAX_DISPATCH(bwd0_chunk_kernel, dim3(n1, nch), ny * sizeof(cplx<T>), G0, bsrc, B[1], cx,
-                      x, nx, ny);
+    // ---- level 0 backward by tridiagonal sweeps (and the kept rows copied)
+    RCI_CUDA_TRY(trs_attr(tri_rows_solve_kernel<T, true>));
+    tri_rows_solve_kernel<T, true><<<(unsigned)ceil_div(n1, TRS_WARPS), 32 * TRS_WARPS,
+                                     trs_smem, s>>>(
+        (const cplx<T>*)h->tdl, (const cplx<T>*)h->tdinv, (const cplx<T>*)h->tdu,
+        (const cplx<T>*)h->tdu2, h->tpiv, bsrc, B[1], cx, x, nx, ny, n1);
+    rci_note_launch();
+    RCI_CUDA_TRY(cudaGetLastError());
 #undef RCI_SMAX_DISPATCH
     return cudaSuccess;
   }
