@@ -709,6 +709,7 @@ def _serve_stream(P, W, local, n_requests, burst, slots, arena_gb, cache_gb, rep
         status_counts[str(r["status"])] = status_counts.get(str(r["status"]), 0) + 1
     span = (max(r["t_end_us"] for r in res) - min(r["t_submit_us"] for r in res)) * 1e-6
     grad = np.array([q.want_grad for q in reqs])
+    fb = np.array([bool(r.get("fp64_fallback", 0)) for r in res])
     delta = ("submitted", "completed", "failed", "admission_waits", "bypasses", "cache_hits",
              "cache_evictions")
     return {
@@ -718,6 +719,8 @@ def _serve_stream(P, W, local, n_requests, burst, slots, arena_gb, cache_gb, rep
         "p50_queue_ms": round(float(np.percentile(wait, 50)), 3),
         "p99_queue_ms": round(float(np.percentile(wait, 99)), 3),
         "p50_ms_gradient": round(float(np.percentile(lat[grad], 50)), 3) if grad.any() else None,
+        "fp64_fallbacks": int(fb.sum()),
+        "p99_ms_fp32_only": round(float(np.percentile(lat[~fb], 99)), 3) if (~fb).any() else None,
         "requests": len(reqs), "failed": len(reqs) - sum(ok), "unconverged": unconverged,
         "status_counts": status_counts, "repeated_designs": round(repeat, 3),
         "arrival_rate_per_s": round(rate, 3), "capacity_evals_per_s": round(capacity, 3),

@@ -355,7 +355,8 @@ typedef struct {
   int32_t cache_hit;      /* 1: a resident factorisation was reused */
   double value;           /* the averaged intensity F */
   int32_t refine_iters;
-  int32_t reserved;
+  int32_t fp64_fallback;  /* 1: the FP32 factorisation could not resolve the design and the
+                             evaluation finished on the FP64 fallback (rci_info.fallback) */
   double rel_residual;
   double t_submit_us;     /* server clock: microseconds since rci_server_create */
   double t_start_us;      /* admitted (grid ready) */

@@ -61,7 +61,7 @@ class RequestC(C.Structure):
 
 class ResultC(C.Structure):
     _fields_ = [("status", C.c_int32), ("cache_hit", C.c_int32), ("value", C.c_double),
-                ("refine_iters", C.c_int32), ("reserved", C.c_int32),
+                ("refine_iters", C.c_int32), ("fp64_fallback", C.c_int32),
                 ("rel_residual", C.c_double), ("t_submit_us", C.c_double),
                 ("t_start_us", C.c_double), ("t_end_us", C.c_double),
                 ("footprint", C.c_uint64)]
@@ -546,7 +546,8 @@ class Server:
         _check(lib().rci_server_wait(self._h, ticket, timeout, C.byref(r)))
         grad = self._grads.pop(ticket, None)
         return {"status": r.status, "value": r.value, "cache_hit": bool(r.cache_hit),
-                "refine_iters": r.refine_iters, "rel_residual": r.rel_residual,
+                "refine_iters": r.refine_iters, "fp64_fallback": r.fp64_fallback,
+                "rel_residual": r.rel_residual,
                 "t_submit_us": r.t_submit_us, "t_start_us": r.t_start_us,
                 "t_end_us": r.t_end_us, "footprint": r.footprint, "grad": grad}
 
