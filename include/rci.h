@@ -419,6 +419,28 @@ uint64_t rci_kernel_launches(void);
 rci_status rci_block_inverse(const void* src, void* out, int64_t n, int64_t batch, int32_t prec,
                              int32_t kernel, void* stream);
 
+/* Batched complex GEMM of the block factorisation (instrumentation and tests; Sec. 4.2
+ * leaves the solver open, and every level >= 1 of block cyclic reduction is built from these
+ * products):
+ *   C[z] = alpha op(A[z]) op(B[z]) + beta C0[z],   z = 0 .. batch-1,
+ * op = identity (ta / tb == 0) or transpose (no conjugation), A[z] op-shaped M x K, B[z]
+ * K x N, C[z] M x N; real alpha, beta.  Row-major DEVICE arrays of complex64 (prec
+ * RCI_FP32_REFINE) or complex128 (RCI_FP64), leading dimensions lda, ldb, ldc0, ldc and element
+ * strides sA, sB, sC0, sC between batch members (in complex elements); C0 may be NULL
+ * (beta ignored).  C may equal C0 (same element positions), no other overlap.
+ * kernel: 0 = the factorisation's dispatch; 1 = tensor cores (3xTF32 tcgen05), operands
+ * staged through registers into shared memory; 2 = tensor cores fed by TMA with the A
+ * operand in tensor memory (needs 2 <= N <= 160 and even, 16-byte aligned A, B, C, C0, even
+ * leading dimensions and, for batch > 1, even positive sA, sB); 3 = SIMT.  Kernels 1 and 2
+ * are FP32 only; the SIMT kernel (3, and 0 where it dispatches there: FP64, or batches too
+ * small to fill the GPU) has no form with both operands transposed.  Synchronises `stream` (cudaStream_t or NULL) and allocates a 4-byte status
+ * word.  Errors: EINVAL (sizes, a kernel that does not apply), ETIMEOUT, ECUDA. */
+rci_status rci_cgemm_batched(int64_t M, int64_t N, int64_t K, int32_t ta, int32_t tb,
+                             double alpha, const void* A, int64_t lda, int64_t sA, const void* B,
+                             int64_t ldb, int64_t sB, double beta, const void* C0, int64_t ldc0,
+                             int64_t sC0, void* C, int64_t ldc, int64_t sC, int64_t batch,
+                             int32_t prec, int32_t kernel, void* stream);
+
 /* Failure detection: every wait of a tensor-core pipeline stage (operand buffers,
  * accumulators) spins at most `cycles` SM clock cycles; a wait that runs out ends its
  * kernel (no trap), which records a device status that the next rci_factor / rci_solve

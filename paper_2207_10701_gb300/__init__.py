@@ -13,7 +13,7 @@ There is no CPU fallback.
 """
 from paper_2207_10701_gb300.rci import (  # noqa: F401
     Grid, RciError, Info, Server, grid_footprint, lib, qform_toeplitz, qform_toeplitz_noalloc, gauss_legendre,
-    kernel_launches, set_wait_limit, measure_peaks, block_inverse, EXPORTED, QFORM_NOALLOC_MAX_N,
+    kernel_launches, set_wait_limit, measure_peaks, block_inverse, cgemm_batched, EXPORTED, QFORM_NOALLOC_MAX_N,
     OBJ_POINT, OBJ_PLANEWAVE, OBJ_VIRTUAL_FOCUS, OBJ_USER_ROW,
     LIGHT_CONE, LIGHT_ANNULUS, LIGHT_USER_LAGS, LIGHT_TABULATED, FP64, FP32_REFINE,
 )

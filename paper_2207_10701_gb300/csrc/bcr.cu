@@ -2081,12 +2081,31 @@ static cudaError_t factor_t(BcrHandle* h, const double2* dg, const double2* cx, 
                          nullptr, 0, 0, X, ny, nn, m, s, h->prof, PF_GEMM, h->status));
     RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, true, one, Dinv, ny, nn, L + 2 * nn, ny, 2 * nn, zero,
                          nullptr, 0, 0, Y, ny, nn, my, s, h->prof, PF_GEMM, h->status));
-    // D'_0 = D_0;  D'_k = D_{2k} - L_{2k} Y_{k-1} (k >= 1);  D'_k -= L_{2k+1}^T X_k (k < m)
-    RCI_CUDA_TRY(cudaMemcpyAsync(Dn, D, nn * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s));
-    RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, false, mone, L + 2 * nn, ny, 2 * nn, Y, ny, nn, one,
-                         D + 2 * nn, ny, 2 * nn, Dn + nn, ny, nn, nk - 1, s, h->prof, PF_GEMM, h->status));
-    RCI_CUDA_TRY(gemm<T>(ny, ny, ny, true, false, mone, L + nn, ny, 2 * nn, X, ny, nn, one, Dn, ny,
-                         nn, Dn, ny, nn, m, s, h->prof, PF_GEMM, h->status));
+    // D'_k = D_{2k} - L_{2k} Y_{k-1} (k >= 1) - L_{2k+1}^T X_k (k < m): on the tensor cores one
+    // product over K = 2 ny per kept row (D' written once); otherwise a copy of D_0 and two
+    // batched products
+    bool fused = false;
+    if constexpr (sizeof(T) == 4) {
+      if (nk >= 2 && my >= 1 && (int64_t)nk * ceil_div(ny, 64) >= 152) {
+        const TcSegment g[2] = {
+            {L, ny, 2 * nn, nk, false, Y, ny, nn, my, false, ny, 0, -1, 1, nk},
+            {L + nn, ny, 2 * nn, m, true, X, ny, nn, m, false, ny, 0, 0, 0, m}};
+        ProfScope ps(h->prof, PF_GEMM, s, 8.0 * ny * (double)nn * (nk - 1 + m),
+                     (double)sizeof(cplx<T>) * nn * (2.0 * (nk - 1 + m) + 2.0 * nk), 1);
+        const cudaError_t e = launch_tc_cgemm_tma_seg(ny, ny, 2, g, -1.f, 1.f, D, ny, 2 * nn, Dn, ny,
+                                                      nn, nk, h->status, tc_wait_limit(), s);
+        if (e == cudaSuccess) fused = true;
+        else if (e != cudaErrorNotSupported) return e;
+      }
+    }
+    if (!fused) {
+      RCI_CUDA_TRY(cudaMemcpyAsync(Dn, D, nn * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s));
+      RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, false, mone, L + 2 * nn, ny, 2 * nn, Y, ny, nn, one,
+                           D + 2 * nn, ny, 2 * nn, Dn + nn, ny, nn, nk - 1, s, h->prof, PF_GEMM,
+                           h->status));
+      RCI_CUDA_TRY(gemm<T>(ny, ny, ny, true, false, mone, L + nn, ny, 2 * nn, X, ny, nn, one, Dn,
+                           ny, nn, Dn, ny, nn, m, s, h->prof, PF_GEMM, h->status));
+    }
     // L'_k = -L_{2k} X_{k-1} (k >= 1)
     RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, false, mone, L + 2 * nn, ny, 2 * nn, X, ny, nn, zero,
                          nullptr, 0, 0, Ln + nn, ny, nn, nk - 1, s, h->prof, PF_GEMM, h->status));
@@ -2347,4 +2366,36 @@ cudaError_t bcr_block_inverse(const void* src, void* out, int n, int batch, int 
   if (kernel == 1) return launch_gj_simt<float>((float2*)src, nn, (float2*)out, nn, n, batch, status, s);
   if (kernel == 2) return launch_tc_gj((const float2*)src, nn, (float2*)out, nn, n, batch, status, s);
   return launch_gj<float>((float2*)src, nn, (float2*)out, nn, n, batch, status, s);
+}
+
+cudaError_t bcr_gemm(int M, int N, int K, bool ta, bool tb, double alpha, const void* A,
+                     int64_t lda, int64_t sA, const void* B, int64_t ldb, int64_t sB, double beta,
+                     const void* C0, int64_t ldc0, int64_t sC0, void* C, int64_t ldc, int64_t sC,
+                     int batch, int prec, int kernel, int32_t* status, cudaStream_t s) {
+  if (prec == RCI_FP64) {
+    if (kernel == 1 || kernel == 2) return cudaErrorInvalidValue;
+    const cplx<double> al{alpha, 0.0}, be{beta, 0.0};
+    return gemm<double>(M, N, K, ta, tb, al, (const double2*)A, lda, sA, (const double2*)B, ldb,
+                        sB, be, (const double2*)C0, ldc0, sC0, (double2*)C, ldc, sC, batch, s);
+  }
+  const float2 al = make_float2((float)alpha, 0.f), be = make_float2((float)beta, 0.f);
+  const float2 *a = (const float2*)A, *b = (const float2*)B, *c0 = (const float2*)C0;
+  float2* c = (float2*)C;
+  switch (kernel) {
+    case 1:
+      return launch_tc_cgemm(M, N, K, ta, tb, al, a, lda, sA, b, ldb, sB, be, c0, ldc0, sC0, c, ldc,
+                             sC, batch, status, s, 1);
+    case 2: {
+      const cudaError_t e = launch_tc_cgemm_tma(M, N, K, ta, tb, (float)alpha, a, lda, sA, b, ldb, sB,
+                                                (float)beta, c0, ldc0, sC0, c, ldc, sC, batch,
+                                                status, tc_wait_limit(), s);
+      return e == cudaErrorNotSupported ? cudaErrorInvalidValue : e;
+    }
+    case 3:  // SIMT: no status word, so the dispatch keeps off the tensor cores
+      return gemm<float>(M, N, K, ta, tb, al, a, lda, sA, b, ldb, sB, be, c0, ldc0, sC0, c, ldc, sC,
+                         batch, s);
+    default:
+      return gemm<float>(M, N, K, ta, tb, al, a, lda, sA, b, ldb, sB, be, c0, ldc0, sC0, c, ldc, sC,
+                         batch, s, nullptr, PF_GEMM, status);
+  }
 }

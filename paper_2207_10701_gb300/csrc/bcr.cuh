@@ -50,3 +50,12 @@ void bcr_set_profiler(BcrHandle* h, Profiler* p);
 // (FP32, n <= 160).  A zero pivot is recorded in *status (device word).
 cudaError_t bcr_block_inverse(const void* src, void* out, int n, int batch, int prec, int kernel,
                               int32_t* status, cudaStream_t s);
+
+// Batched complex GEMM C[z] = alpha op(A[z]) op(B[z]) + beta C0[z] (real alpha, beta; prec as
+// the handle's; C0 may be null): kernel 0 = the factorisation's dispatch, 1 = tensor cores
+// with register-staged operands, 2 = tensor cores fed by TMA with A in tensor memory,
+// 3 = SIMT.  An expired wait is recorded as DEV_TIMEOUT in *status (device word).
+cudaError_t bcr_gemm(int M, int N, int K, bool ta, bool tb, double alpha, const void* A,
+                     int64_t lda, int64_t sA, const void* B, int64_t ldb, int64_t sB, double beta,
+                     const void* C0, int64_t ldc0, int64_t sC0, void* C, int64_t ldc, int64_t sC,
+                     int batch, int prec, int kernel, int32_t* status, cudaStream_t s);

@@ -1276,6 +1276,39 @@ rci_status rci_block_inverse(const void* src, void* out, int64_t n, int64_t batc
   return RCI_OK;
 }
 
+rci_status rci_cgemm_batched(int64_t M, int64_t N, int64_t K, int32_t ta, int32_t tb,
+                             double alpha, const void* A, int64_t lda, int64_t sA, const void* B,
+                             int64_t ldb, int64_t sB, double beta, const void* C0, int64_t ldc0,
+                             int64_t sC0, void* C, int64_t ldc, int64_t sC, int64_t batch,
+                             int32_t prec, int32_t kernel, void* stream) {
+  const int64_t lim = 1 << 20;
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || M > lim || N > lim || K > lim || batch < 1 ||
+      batch > 65535 || kernel < 0 || kernel > 3 || (prec != RCI_FP64 && prec != RCI_FP32_REFINE))
+    return RCI_EINVAL;
+  if (!std::isfinite(alpha) || !std::isfinite(beta)) return RCI_EINVAL;
+  const int64_t am = ta ? K : M, ak = ta ? M : K, bk = tb ? N : K, bn = tb ? K : N;
+  if (lda < ak || ldb < bn || ldc < N || sA < 0 || sB < 0 || sC < 0 || (C0 && (ldc0 < N || sC0 < 0)))
+    return RCI_EINVAL;
+  (void)am;
+  (void)bk;
+  if (prec == RCI_FP64 && (kernel == 1 || kernel == 2)) return RCI_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t* st = nullptr;
+  int32_t h = 0;
+  cudaError_t e = cudaMalloc((void**)&st, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(int32_t), s);
+  if (e == cudaSuccess)
+    e = bcr_gemm((int)M, (int)N, (int)K, ta != 0, tb != 0, alpha, A, lda, sA, B, ldb, sB,
+                 C0 ? beta : 0.0, C0, ldc0, sC0, C, ldc, sC, (int)batch, prec, kernel, st, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, st, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(st);
+  if (e == cudaErrorInvalidValue) return RCI_EINVAL;
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? RCI_ENOMEM : RCI_ECUDA;
+  if (h == DEV_TIMEOUT) return RCI_ETIMEOUT;
+  return h == DEV_OK ? RCI_OK : RCI_ECUDA;
+}
+
 int64_t rci_set_wait_limit(int64_t cycles) {
   const long long old = tc_wait_limit();
   tc_set_wait_limit((long long)cycles);

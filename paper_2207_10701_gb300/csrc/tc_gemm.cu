@@ -12,10 +12,12 @@
 // A_hi B_hi + A_hi B_lo + A_lo B_hi in FP32 (the missing A_lo B_lo term is ~2^-22
 // relative).  The solver's FP64 iterative refinement absorbs the rest.
 //
-// Two kernels.  For real alpha and beta and N <= 160 (every product of the block solver)
-// the persistent stacked form below: one CTA per SM, warp-specialised (operand staging,
-// MMA issue, epilogue), 128-row tiles of the stacked product, accumulators double
-// buffered in tensor memory.  Otherwise the expanded-B form: one CTA per 128 x 80 complex
+// Three kernels.  For real alpha and beta, even N <= 160 and 16-byte aligned operands
+// (every product of the block solver) the TMA-fed kernel of tc_gemm_tma.cu, with the A
+// operand in tensor memory.  Where its alignment rules fail, the persistent stacked form
+// below: one CTA per SM, warp-specialised (register-staged operands, MMA issue, epilogue),
+// 128-row tiles of the stacked product, accumulators double buffered in tensor memory.
+// Otherwise (complex scalars, larger N) the expanded-B form: one CTA per 128 x 80 complex
 // output tile (M = 128 rows, N = 160 real columns per MMA); K in chunks of 8 complex (16
 // real) per pipeline stage, 3 stages (two CTAs per SM).  All 256 threads stage operands
 // (global -> registers, issued ahead -> split -> shared memory in the K-major, no-swizzle
@@ -829,7 +831,8 @@ void tc_set_wait_limit(long long cycles) {
 cudaError_t launch_tc_cgemm(int M, int N, int K, bool ta, bool tb, float2 alpha, const float2* A,
                             int64_t lda, int64_t sA, const float2* B, int64_t ldb, int64_t sB,
                             float2 beta, const float2* C0, int64_t ldc0, int64_t sC0, float2* C,
-                            int64_t ldc, int64_t sC, int batch, int32_t* status, cudaStream_t s) {
+                            int64_t ldc, int64_t sC, int batch, int32_t* status, cudaStream_t s,
+                            int variant) {
   if (batch <= 0) return cudaSuccess;
   if (batch > 65535 || M < 1 || N < 1 || K < 1) return cudaErrorInvalidValue;
   TcArgs a{M,   N,   K,    A,   lda,   sA,   B,      ldb,   sB, C, ldc, sC, C0,
@@ -843,6 +846,12 @@ cudaError_t launch_tc_cgemm(int M, int N, int K, bool ta, bool tb, float2 alpha,
     return cudaGetLastError();
   };
   if (N <= TNS && alpha.y == 0.f && beta.y == 0.f) {  // real scalars: the stacked form
+    if (variant == 0) {
+      const cudaError_t e =
+          launch_tc_cgemm_tma(M, N, K, ta, tb, alpha.x, A, lda, sA, B, ldb, sB, beta.x, C0, ldc0,
+                              sC0, C, ldc, sC, batch, status, tc_wait_limit(), s);
+      if (e != cudaErrorNotSupported) return e;
+    }
     // persistent: one CTA per SM (or per tile, when there are fewer)
     const int nsm = sm_count();
     const int64_t ntiles = (int64_t)batch * ceil_div(2 * (int64_t)M, TM);

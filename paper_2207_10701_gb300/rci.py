@@ -153,6 +153,10 @@ EXPORTED = {
     "rci_kernel_launches": (C.c_uint64, []),
     "rci_set_wait_limit": (C.c_int64, [C.c_int64]),
     "rci_block_inverse": (C.c_int, [_P, _P, C.c_int64, C.c_int64, C.c_int32, C.c_int32, _P]),
+    "rci_cgemm_batched": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_int32,
+                                    C.c_double, _P, C.c_int64, C.c_int64, _P, C.c_int64,
+                                    C.c_int64, C.c_double, _P, C.c_int64, C.c_int64, _P,
+                                    C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_int32, _P]),
     "rci_measure_peaks": (C.c_int, [C.c_int, C.POINTER(PeaksC)]),
     "rci_status_str": (C.c_char_p, [C.c_int]),
     "rci_last_error": (C.c_char_p, [_P]),
@@ -450,6 +454,36 @@ def block_inverse(blocks, kernel: int = 0, stream=None):
     prec = FP32_REFINE if src.dtype == torch.complex64 else FP64
     _check(lib().rci_block_inverse(_dptr(src), _dptr(out), src.shape[1], src.shape[0], prec,
                                    kernel, _stream(stream)))
+    return out
+
+
+def cgemm_batched(A, B, C0=None, alpha: float = 1.0, beta: float = 0.0, ta: bool = False,
+                  tb: bool = False, kernel: int = 0, out=None, stream=None):
+    """C[z] = alpha op(A[z]) op(B[z]) + beta C0[z] with the factorisation's batched complex
+    GEMM kernels (rci_cgemm_batched): CUDA tensors [batch, rows, cols] of complex64 or
+    complex128 whose rows are contiguous (any row and batch strides); op = transpose when ta
+    / tb.  kernel 0 = the factorisation's dispatch, 1 = tensor cores with register-staged
+    operands, 2 = tensor cores fed by TMA, 3 = SIMT.  Returns C (`out` when given)."""
+    torch = _torch()
+    for t in (A, B) + ((C0,) if C0 is not None else ()):
+        if t.dim() != 3 or not t.is_cuda or t.stride(2) != 1:
+            raise ValueError("operands: CUDA tensors [batch, rows, cols] with contiguous rows")
+        if t.dtype != A.dtype or t.dtype not in (torch.complex64, torch.complex128):
+            raise TypeError("complex64 or complex128 operands of one type")
+    batch = A.shape[0]
+    M = A.shape[2] if ta else A.shape[1]
+    K = A.shape[1] if ta else A.shape[2]
+    N = B.shape[1] if tb else B.shape[2]
+    if (B.shape[2] if tb else B.shape[1]) != K or B.shape[0] != batch:
+        raise ValueError("shapes do not chain")
+    if out is None:
+        out = torch.empty((batch, M, N), dtype=A.dtype, device=A.device)
+    prec = FP32_REFINE if A.dtype == torch.complex64 else FP64
+    c0p, ldc0, sc0 = (None, 0, 0) if C0 is None else (_dptr(C0), C0.stride(1), C0.stride(0))
+    _check(lib().rci_cgemm_batched(M, N, K, int(ta), int(tb), float(alpha), _dptr(A), A.stride(1),
+                                   A.stride(0), _dptr(B), B.stride(1), B.stride(0), float(beta),
+                                   c0p, ldc0, sc0, _dptr(out), out.stride(1), out.stride(0), batch,
+                                   prec, kernel, _stream(stream)))
     return out
 
 
