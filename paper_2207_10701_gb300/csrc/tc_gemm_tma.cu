@@ -20,20 +20,23 @@
 //
 // Roles of one persistent CTA (one per SM, 14 warps), over the CTA's tiles (tile = product
 // z x 64-row block) and their K stages of 8 complex k:
-//   warp 12    (one lane) TMA: raw A (64 rows x 8 k, or 8 k x 64 rows for op = T) and raw
-//              B (8 k x N, or N x 8 k) into a ring of raw stages, completion by mbarrier
-//              transaction count;
+//   warp 12    TMA: raw A (64 rows x 8 k, or 8 k x 64 rows for op = T) and raw B (8 k x N,
+//              or N x 8 k) into a ring of raw stages, completion by mbarrier transaction
+//              count (one lane issues);
 //   warps 0-7  convert: warp w writes tensor-memory lanes 32 (w % 4) .. + 31 for half of
 //              the stage's k: each lane builds its stacked row, splits it and stores hi and
-//              lo into the stage's tensor-memory A slot (tcgen05.st); all 256 threads split
-//              B into the stage's shared-memory slot (K-major core matrices);
-//   warp 13    (one lane) waits for a converted stage, issues its six MMAs (A from tensor
+//              lo into the stage's tensor-memory A slot (tcgen05.st); all eight warps split
+//              B (up to three items per thread) into the stage's shared-memory slot (K-major
+//              core matrices), every load of a thread issued before its stores;
+//   warp 13    waits for a converted stage; one lane issues its six MMAs (A from tensor
 //              memory, B from shared memory) and commits them to the stage's "empty"
 //              barrier; after a tile, to the accumulator's "full" barrier;
-//   warps 8-11 epilogue: read 16 accumulator columns at a time (warp 8 + w: lanes
-//              32 w ..), exchange Re / Im with the neighbouring lane and store 16-byte
-//              pieces (two complex) so that each lane pair writes one full 32-byte sector;
-//              C0 of the next chunk is loaded while the current one is stored.
+//   warps 8-11 epilogue: read 16 accumulator columns at a time (warp w: lanes
+//              32 (w % 4) ..), exchange Re / Im with the neighbouring lane and store
+//              16-byte pieces (two complex) so that each lane pair writes one full 32-byte
+//              sector; C0 of the next chunk is loaded while the current one is stored.
+// Every role waits as a whole warp (a lane-0 poll with the other lanes parked at a shuffle
+// costed several hundred cycles per wait, even on a completed barrier).
 // Two accumulators (tensor-memory columns 0 and 256) let a tile's epilogue run under the
 // next tile's MMAs; the converted-stage A slots sit in the columns between.
 // Every wait is bounded; the first that runs out sets a shared abort flag that ends the
@@ -59,9 +62,13 @@ constexpr int TT_NMAX = 160;      // largest N (complex columns)
 #endif
 constexpr int TT_RS = RCI_TMA_RAW_STAGES;    // raw stages (TMA in flight)
 constexpr int TT_CS = RCI_TMA_CONV_STAGES;   // converted stages (tensor-memory A slot + B)
+// warps 0-7 convert A (two per tensor-memory lane quarter) and B (ten converter warps, two
+// of them on B only, measured no faster)
+constexpr int TT_AWARPS = 8;
 constexpr int TT_CONV_WARPS = 8, TT_EPI_WARP0 = 8, TT_TMA_WARP = 12, TT_MMA_WARP = 13;
 constexpr int TT_THREADS = 14 * 32;
 constexpr int TT_CONV_THREADS = 32 * TT_CONV_WARPS;
+constexpr int TT_BITEMS = (TT_NMAX * 4 + TT_CONV_THREADS - 1) / TT_CONV_THREADS;  // 3
 constexpr uint32_t TT_RAW_A = TT_ROWS * TT_KC * 8;        // 4096 bytes
 constexpr uint32_t TT_RAW_B = TT_NMAX * TT_KC * 8;        // 10240 bytes (N = 160)
 constexpr uint32_t TT_RAW_STAGE = TT_RAW_A + TT_RAW_B;    // 14336 = 14 x 1024
@@ -76,7 +83,7 @@ constexpr size_t TT_SMEM = TT_BAR_OFF + (size_t)TT_NBAR * 8 + 16;
 static_assert(TT_RAW_STAGE % 1024 == 0 && TT_RAW_A % 1024 == 0, "swizzled TMA destinations");
 static_assert(TT_CONV_OFF % 1024 == 0 && TT_CSTAGE % 1024 == 0, "operand alignment");
 static_assert(TT_SMEM <= 227 * 1024, "one CTA per SM");
-static_assert(TT_NMAX * 4 <= 3 * TT_CONV_THREADS, "three B items per converter thread");
+static_assert(TT_NMAX * 4 <= TT_BITEMS * TT_CONV_THREADS, "B items per converter thread");
 // tensor-memory columns: accumulators, then the A slots (hi in 16 columns, lo in the next 16)
 constexpr uint32_t TT_TMEM_COLS = 512;
 constexpr uint32_t TT_ACC_STRIDE = 256;  // accumulator b at column 256 b
@@ -141,6 +148,12 @@ __device__ __forceinline__ uint32_t sw64_addr(uint32_t tile, int r, int c) {
   return row + (((uint32_t)c ^ (row >> 7)) & 3u) * 16u;
 }
 
+__device__ __forceinline__ void sts128(uint32_t a, const float (&v)[4]) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v[0]), "f"(v[1]), "f"(v[2]),
+               "f"(v[3])
+               : "memory");
+}
+
 __device__ __forceinline__ float4 lds128(uint32_t a) {
   float4 v;
   asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
@@ -185,21 +198,6 @@ __device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t parity) {
   return done != 0u;
 }
 
-// bounded wait that also ends when another role has given up
-__device__ __forceinline__ bool tt_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                        long long limit) {
-  const uint32_t a = smem_u32(bar);
-  const long long t0 = clock64();
-  while (true) {
-    if (mbar_test(a, parity)) return true;
-    if (*abort_flag) return false;
-    if (clock64() - t0 > limit) {
-      *abort_flag = 1;
-      return false;
-    }
-  }
-}
-
 // bounded wait that ignores the abort flag (the kernel's own copies and MMAs before exit)
 __device__ __forceinline__ bool tt_wait_own(uint64_t* bar, uint32_t parity) {
   const uint32_t a = smem_u32(bar);
@@ -210,12 +208,20 @@ __device__ __forceinline__ bool tt_wait_own(uint64_t* bar, uint32_t parity) {
   }
 }
 
-// lane 0 waits, the warp follows its verdict
+// bounded wait taken by the whole warp together (no divergence): the phase has completed
+// once any lane sees it complete; the warp gives up together on the abort flag or the limit
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          long long limit, int lane) {
-  bool got = true;
-  if (lane == 0) got = tt_wait(bar, parity, abort_flag, limit);
-  return __shfl_sync(0xffffffffu, got, 0);
+                                          long long limit) {
+  const uint32_t a = smem_u32(bar);
+  const long long t0 = clock64();
+  while (true) {
+    if (__any_sync(0xffffffffu, mbar_test(a, parity))) return true;
+    const bool expired = clock64() - t0 > limit;
+    if (__any_sync(0xffffffffu, expired || *abort_flag != 0)) {
+      if (expired) *abort_flag = 1;
+      return false;
+    }
+  }
 }
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
@@ -333,7 +339,8 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
 
   if (warp == TT_TMA_WARP) {
     // ------------------------------------------------------------ TMA producer
-    if (lane == 0) {
+    // (the warp waits together; lane 0 issues the copies)
+    {
       const uint32_t bytes = TT_RAW_A + (uint32_t)NB * TT_KC * 8u;
       int it = 0;
       bool ok = true;
@@ -346,10 +353,11 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
         for (int st = 0; st < nst; ++st, ++it) {
           const int s = it % TT_RS;
           if (it >= TT_RS &&
-              !tt_wait(&raw_empty[s], (uint32_t)((it / TT_RS - 1) & 1), abort_flag, p.wait_limit)) {
+              !warp_wait(&raw_empty[s], (uint32_t)((it / TT_RS - 1) & 1), abort_flag, p.wait_limit)) {
             ok = false;
             break;
           }
+          if (lane != 0) continue;
           const bool g1 = !v0 || st >= p.seg[0].nkb;
           const int k0 = (g1 ? (v0 ? st - p.seg[0].nkb : st) : st) * TT_KC;
           unsigned char* rs = sm_raw + (size_t)s * TT_RAW_STAGE;
@@ -370,17 +378,32 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
           }
         }
       }
-      // the copies this thread issued land before the CTA can exit
-      for (int d = it - TT_RS < 0 ? 0 : it - TT_RS; d < it; ++d)
-        if (!tt_wait_own(&raw_full[d % TT_RS], (uint32_t)((d / TT_RS) & 1))) *abort_flag = 1;
+      // the copies lane 0 issued land before the CTA can exit
+      if (lane == 0)
+        for (int d = it - TT_RS < 0 ? 0 : it - TT_RS; d < it; ++d)
+          if (!tt_wait_own(&raw_full[d % TT_RS], (uint32_t)((d / TT_RS) & 1))) *abort_flag = 1;
     }
     __syncwarp();
   } else if (warp < TT_CONV_WARPS) {
     // ------------------------------------------------------------ converters
-    const int q = warp & 3, kh = warp >> 2;
+    const int q = warp & 3, kh = (warp >> 2) & 1;  // (kh: for the A warps 0-7)
     const int l = 16 * q + (lane >> 1);  // complex row of the tile
     const int part = lane & 1;           // 0: (ar, -ai) -> Re rows; 1: (ai, ar) -> Im rows
     const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+    // this thread's B items e = tid + 256 r: column n, pair j of complex k (2 j, 2 j + 1);
+    // packed n | j << 16 (-1: none), the raw-tile read index (op = N) and the offset in the
+    // split stage
+    int bitem[TT_BITEMS], brd[TT_BITEMS];
+    uint32_t boff[TT_BITEMS];
+#pragma unroll
+    for (int r = 0; r < TT_BITEMS; ++r) {
+      const int e = tid + TT_CONV_THREADS * r;
+      const int j = e / NB, n = e - j * NB;
+      const bool v = e < 4 * NB;
+      bitem[r] = v ? (n | (j << 16)) : -1;
+      brd[r] = (2 * j) * NB + n;
+      boff[r] = bcore_off(n, 4 * j);
+    }
     int it = 0;
     bool ok = true;
     for (int tl = 0; tl < ntl && ok; ++tl) {
@@ -391,67 +414,70 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
         const bool g1 = !v0 || st >= p.seg[0].nkb;
         const bool ta = g1 ? TA1 : TA0, tb = g1 ? TB1 : TB0;
         const int s = it % TT_RS, cs = it % TT_CS;
-        if (!warp_wait(&raw_full[s], (uint32_t)((it / TT_RS) & 1), abort_flag, p.wait_limit, lane)) {
+        if (!warp_wait(&raw_full[s], (uint32_t)((it / TT_RS) & 1), abort_flag, p.wait_limit)) {
           ok = false;
           break;
         }
         if (it >= TT_CS && !warp_wait(&conv_empty[cs], (uint32_t)((it / TT_CS - 1) & 1), abort_flag,
-                                      p.wait_limit, lane)) {
+                                      p.wait_limit)) {
           ok = false;
           break;
         }
         fence_after();
         const unsigned char* rs = sm_raw + (size_t)s * TT_RAW_STAGE;
-        // A: four complex k of row l
-        float2 a[4];
-        if (!ta) {
+        if (warp < TT_AWARPS) {
+          // A: four complex k of row l
+          float2 a[4];
+          if (!ta) {
 #pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            const float4 v = lds128(sw64_addr(smem_u32(rs), l, 2 * kh + c));
-            a[2 * c] = make_float2(v.x, v.y);
-            a[2 * c + 1] = make_float2(v.z, v.w);
-          }
-        } else {
-          const float2* ra = reinterpret_cast<const float2*>(rs);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) a[j] = ra[(4 * kh + j) * TT_ROWS + l];
-        }
-        float hi[8], lo[8];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const float x0 = part ? a[j].y : a[j].x;
-          const float x1 = part ? a[j].x : -a[j].y;
-          split_tf32(x0, hi[2 * j], lo[2 * j]);
-          split_tf32(x1, hi[2 * j + 1], lo[2 * j + 1]);
-        }
-        const uint32_t slot = lane_base + a_slot(cs) + 8u * (uint32_t)kh;
-        tmem_st8(slot, hi);
-        tmem_st8(slot + 16u, lo);
-        // B: (n, j) items, real k 4 j .. 4 j + 3 = complex k 2 j, 2 j + 1 of column n
-        const unsigned char* rb = rs + TT_RAW_A;
-        unsigned char* bs = sm_raw + TT_CONV_OFF + (size_t)cs * TT_CSTAGE;
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          const int e = tid + TT_CONV_THREADS * r;
-          if (e < 4 * NB) {
-            const int j = e / NB, n = e - j * NB;
-            float4 v;
-            if (!tb) {
-              const float2* rbb = reinterpret_cast<const float2*>(rb);
-              const float2 b0 = rbb[(2 * j) * NB + n], b1 = rbb[(2 * j + 1) * NB + n];
-              v = make_float4(b0.x, b0.y, b1.x, b1.y);
-            } else {
-              v = lds128(sw64_addr(smem_u32(rb), n, j));
+            for (int c = 0; c < 2; ++c) {
+              const float4 v = lds128(sw64_addr(smem_u32(rs), l, 2 * kh + c));
+              a[2 * c] = make_float2(v.x, v.y);
+              a[2 * c + 1] = make_float2(v.z, v.w);
             }
-            float h[4], o[4];
-            split_tf32(v.x, h[0], o[0]);
-            split_tf32(v.y, h[1], o[1]);
-            split_tf32(v.z, h[2], o[2]);
-            split_tf32(v.w, h[3], o[3]);
-            const uint32_t off = bcore_off(n, 4 * j);
-            *reinterpret_cast<float4*>(bs + off) = make_float4(h[0], h[1], h[2], h[3]);
-            *reinterpret_cast<float4*>(bs + TT_BSPLIT + off) = make_float4(o[0], o[1], o[2], o[3]);
+          } else {
+            const float2* ra = reinterpret_cast<const float2*>(rs);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) a[j] = ra[(4 * kh + j) * TT_ROWS + l];
           }
+          float hi[8], lo[8];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float x0 = part ? a[j].y : a[j].x;
+            const float x1 = part ? a[j].x : -a[j].y;
+            split_tf32(x0, hi[2 * j], lo[2 * j]);
+            split_tf32(x1, hi[2 * j + 1], lo[2 * j + 1]);
+          }
+          const uint32_t slot = lane_base + a_slot(cs) + 8u * (uint32_t)kh;
+          tmem_st8(slot, hi);
+          tmem_st8(slot + 16u, lo);
+        }
+        // B: this thread's (n, j) items, all loads first, then the splits and stores
+        const unsigned char* rb = rs + TT_RAW_A;
+        const uint32_t rbu = smem_u32(rb);
+        const uint32_t bsu = smem_u32(sm_raw + TT_CONV_OFF + (size_t)cs * TT_CSTAGE);
+        float4 bv[TT_BITEMS];
+#pragma unroll
+        for (int r = 0; r < TT_BITEMS; ++r) {
+          if (bitem[r] < 0) continue;
+          if (!tb) {
+            const float2* rbb = reinterpret_cast<const float2*>(rb);
+            const float2 b0 = rbb[brd[r]], b1 = rbb[brd[r] + NB];
+            bv[r] = make_float4(b0.x, b0.y, b1.x, b1.y);
+          } else {
+            bv[r] = lds128(sw64_addr(rbu, bitem[r] & 0xFFFF, bitem[r] >> 16));
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < TT_BITEMS; ++r) {
+          if (bitem[r] < 0) continue;
+          float h[4], o[4];
+          split_tf32(bv[r].x, h[0], o[0]);
+          split_tf32(bv[r].y, h[1], o[1]);
+          split_tf32(bv[r].z, h[2], o[2]);
+          split_tf32(bv[r].w, h[3], o[3]);
+          sts128(bsu + boff[r], h);
+          sts128(bsu + TT_BSPLIT + boff[r], o);
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -465,28 +491,29 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
     }
   } else if (warp == TT_MMA_WARP) {
     // ------------------------------------------------------------ MMA issue
-    if (lane == 0) {
-      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NB >> 3) << 17) |
-                             ((uint32_t)(128 >> 4) << 24);
-      bool ok = true;
-      int it = 0;
-      for (int tl = 0; tl < ntl && ok; ++tl) {
-        const int b = tl & 1;
-        if (tl >= 2 &&
-            !tt_wait(&acc_empty[b], (uint32_t)((tl / 2 - 1) & 1), abort_flag, p.wait_limit))
+    // (the warp waits together; lane 0 issues the MMAs and commits)
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NB >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);
+    bool ok = true;
+    int it = 0;
+    for (int tl = 0; tl < ntl && ok; ++tl) {
+      const int b = tl & 1;
+      if (tl >= 2 &&
+          !warp_wait(&acc_empty[b], (uint32_t)((tl / 2 - 1) & 1), abort_flag, p.wait_limit))
+        break;
+      fence_after();
+      const uint32_t acc = tmem + (uint32_t)b * TT_ACC_STRIDE;
+      const int z = ((int)blockIdx.x + tl * (int)gridDim.x) / mt;
+      bool v0, v1;
+      const int nst = tile_stages(p, z, v0, v1);
+      for (int st = 0; st < nst; ++st, ++it) {
+        const int cs = it % TT_CS;
+        if (!warp_wait(&conv_full[cs], (uint32_t)((it / TT_CS) & 1), abort_flag, p.wait_limit)) {
+          ok = false;
           break;
+        }
         fence_after();
-        const uint32_t acc = tmem + (uint32_t)b * TT_ACC_STRIDE;
-        const int z = ((int)blockIdx.x + tl * (int)gridDim.x) / mt;
-        bool v0, v1;
-        const int nst = tile_stages(p, z, v0, v1);
-        for (int st = 0; st < nst; ++st, ++it) {
-          const int cs = it % TT_CS;
-          if (!tt_wait(&conv_full[cs], (uint32_t)((it / TT_CS) & 1), abort_flag, p.wait_limit)) {
-            ok = false;
-            break;
-          }
-          fence_after();
+        if (lane == 0) {
           const uint32_t aslot = tmem + a_slot(cs);
           const uint32_t bh = smem_u32(sm_raw + TT_CONV_OFF + (size_t)cs * TT_CSTAGE);
           const uint32_t bl = bh + TT_BSPLIT;
@@ -500,16 +527,20 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
           }
           mma_commit(&conv_empty[cs]);
         }
-        if (ok) mma_commit(&acc_full[b]);
+        __syncwarp();
       }
-      // every MMA issued by this thread has finished before the tensor memory is freed
+      if (ok && lane == 0) mma_commit(&acc_full[b]);
+      __syncwarp();
+    }
+    // every MMA issued by lane 0 has finished before the tensor memory is freed
+    if (lane == 0) {
       mma_commit(done_bar);
       if (!tt_wait_own(done_bar, 0)) *abort_flag = 1;
     }
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue
-    const int q = warp - TT_EPI_WARP0;  // == warp % 4: the lanes this warp may read
+    const int q = warp & 3;  // a warp may read tensor-memory lanes 32 (warp % 4) .. + 31
     const int l = 16 * q + (lane >> 1);
     const int part = lane & 1;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
@@ -536,7 +567,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
       };
       float4 c0a[4], c0b[4];
       load_c0(0, c0a);
-      if (!warp_wait(&acc_full[b], (uint32_t)((tl / 2) & 1), abort_flag, p.wait_limit, lane)) break;
+      if (!warp_wait(&acc_full[b], (uint32_t)((tl / 2) & 1), abort_flag, p.wait_limit)) break;
       fence_after();
       bool v0, v1;
       const bool empty = tile_stages(p, z, v0, v1) == 0;  // no MMA: the product is zero
