@@ -198,8 +198,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
       : "memory");
 }
 
-// bounded wait that also ends when another warp has given up
-__device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, long long limit,
+// bounded wait taken by a whole warp together (no lane parked at a shuffle while one lane
+// polls, which costs several hundred cycles per wait), ending early when another warp has
+// given up: the phase has completed once any
+// lane sees it complete; the warp gives up together on the abort flag or the limit
+__device__ __forceinline__ bool warp_wait_ab(uint64_t* bar, uint32_t parity, long long limit,
                                              volatile int* abort_flag) {
   const uint32_t a = smem_u32(bar);
   const long long t0 = clock64();
@@ -211,10 +214,10 @@ __device__ __forceinline__ bool mbar_wait_ab(uint64_t* bar, uint32_t parity, lon
         : "=r"(done)
         : "r"(a), "r"(parity)
         : "memory");
-    if (done) return true;
-    if (*abort_flag) return false;
-    if (clock64() - t0 > limit) {
-      *abort_flag = 1;
+    if (__any_sync(0xffffffffu, done != 0u)) return true;
+    const bool expired = clock64() - t0 > limit;
+    if (__any_sync(0xffffffffu, expired || *abort_flag != 0)) {
+      if (expired) *abort_flag = 1;
       return false;
     }
   }
@@ -416,8 +419,8 @@ __global__ void __launch_bounds__(GJT_THREADS, 1) tc_gj_kernel(GjtArgs p) {
     fence_after();
 
     if (mma_warp) {
-      // ---------------------------------------------- MMA issue (one lane)
-      if (l == 0) {
+      // ---------------------------------------------- MMA issue (the warp waits, one lane issues)
+      {
         const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo);
         const uint32_t bh = smem_u32(Bhi), bl = smem_u32(Blo);
         auto range = [&](int j0, int j1) {
@@ -439,20 +442,23 @@ __global__ void __launch_bounds__(GJT_THREADS, 1) tc_gj_kernel(GjtArgs p) {
           const bool has_next = P + 1 < npanel;
           const int h1 = has_next ? c0 + 2 * GJT_NB : c0 + GJT_NB;
           const bool bulk_lo = c0 > 0, bulk_hi = h1 < np;
-          if (!mbar_wait_ab(bar_ops, nops & 1u, p.wait_limit, abort_flag)) {
+          if (!warp_wait_ab(bar_ops, nops & 1u, p.wait_limit, abort_flag)) {
             ok = false;
             break;
           }
           ++nops;
           fence_after();
-          if (has_next) {
-            range(c0 + GJT_NB, h1);
-            mma_commit(bar_head);
+          if (l == 0) {
+            if (has_next) {
+              range(c0 + GJT_NB, h1);
+              mma_commit(bar_head);
+            }
+            if (bulk_lo) range(0, c0);
+            if (bulk_hi) range(h1, np);
+            if (bulk_lo || bulk_hi) mma_commit(bar_bulk);
+            if (has_next || bulk_lo || bulk_hi) mma_issued = true;
           }
-          if (bulk_lo) range(0, c0);
-          if (bulk_hi) range(h1, np);
-          if (bulk_lo || bulk_hi) mma_commit(bar_bulk);
-          if (has_next || bulk_lo || bulk_hi) mma_issued = true;
+          __syncwarp();
         }
       }
       __syncwarp();
@@ -495,11 +501,9 @@ __global__ void __launch_bounds__(GJT_THREADS, 1) tc_gj_kernel(GjtArgs p) {
           tmem_st16(taddr(2, c0), v);
         }
       };
-      // lane 0 waits (bounded, abort-aware), the warp follows, the panel warps agree
+      // each warp waits (bounded, abort-aware) as a whole, then the panel warps agree
       auto wait_all = [&](uint64_t* bar, uint32_t& cnt) -> bool {
-        bool got = true;
-        if (l == 0) got = mbar_wait_ab(bar, cnt & 1u, p.wait_limit, abort_flag);
-        got = __shfl_sync(FULL, got, 0);
+        const bool got = warp_wait_ab(bar, cnt & 1u, p.wait_limit, abort_flag);
         ++cnt;
         const bool all = pbar_and(got);
         fence_after();
