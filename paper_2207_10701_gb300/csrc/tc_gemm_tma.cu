@@ -23,11 +23,11 @@
 //   warp 12    TMA: raw A (64 rows x 8 k, or 8 k x 64 rows for op = T) and raw B (8 k x N,
 //              or N x 8 k) into a ring of raw stages, completion by mbarrier transaction
 //              count (one lane issues);
-//   warps 0-7  convert: warp w writes tensor-memory lanes 32 (w % 4) .. + 31 for half of
-//              the stage's k: each lane builds its stacked row, splits it and stores hi and
-//              lo into the stage's tensor-memory A slot (tcgen05.st); all eight warps split
-//              B (up to three items per thread) into the stage's shared-memory slot (K-major
-//              core matrices), every load of a thread issued before its stores;
+//   warps 0-7  convert, in two groups of four that take the stages in turn: warp w writes
+//              tensor-memory lanes 32 (w % 4) .. + 31: each lane builds its stacked row,
+//              splits it and stores hi and lo into the stage's tensor-memory A slot
+//              (tcgen05.st); the group's threads split B (five items each) into the stage's
+//              shared-memory slot (K-major core matrices), all loads before the stores;
 //   warp 13    waits for a converted stage; one lane issues its six MMAs (A from tensor
 //              memory, B from shared memory) and commits them to the stage's "empty"
 //              barrier; after a tile, to the accumulator's "full" barrier;
@@ -62,13 +62,20 @@ constexpr int TT_NMAX = 160;      // largest N (complex columns)
 #endif
 constexpr int TT_RS = RCI_TMA_RAW_STAGES;    // raw stages (TMA in flight)
 constexpr int TT_CS = RCI_TMA_CONV_STAGES;   // converted stages (tensor-memory A slot + B)
-// warps 0-7 convert A (two per tensor-memory lane quarter) and B (ten converter warps, two
-// of them on B only, measured no faster)
-constexpr int TT_AWARPS = 8;
+// Eight converter warps in TT_GROUPS groups that take the K stages in turn (group g the
+// stages it with it % TT_GROUPS == g), so that one group's waits and fences overlap the
+// other's work; a group has a warp (or two) per tensor-memory lane quarter.
+#ifndef RCI_TMA_CONV_GROUPS
+#define RCI_TMA_CONV_GROUPS 2
+#endif
+constexpr int TT_GROUPS = RCI_TMA_CONV_GROUPS;
 constexpr int TT_CONV_WARPS = 8, TT_EPI_WARP0 = 8, TT_TMA_WARP = 12, TT_MMA_WARP = 13;
 constexpr int TT_THREADS = 14 * 32;
-constexpr int TT_CONV_THREADS = 32 * TT_CONV_WARPS;
-constexpr int TT_BITEMS = (TT_NMAX * 4 + TT_CONV_THREADS - 1) / TT_CONV_THREADS;  // 3
+constexpr int TT_GWARPS = TT_CONV_WARPS / TT_GROUPS;      // warps per group
+constexpr int TT_GTHREADS = 32 * TT_GWARPS;
+constexpr int TT_KSPLIT = TT_GWARPS / 4;                  // warps per lane quarter in a group
+constexpr int TT_BITEMS = (TT_NMAX * 4 + TT_GTHREADS - 1) / TT_GTHREADS;
+static_assert(TT_GWARPS % 4 == 0 && (TT_KSPLIT == 1 || TT_KSPLIT == 2), "group shape");
 constexpr uint32_t TT_RAW_A = TT_ROWS * TT_KC * 8;        // 4096 bytes
 constexpr uint32_t TT_RAW_B = TT_NMAX * TT_KC * 8;        // 10240 bytes (N = 160)
 constexpr uint32_t TT_RAW_STAGE = TT_RAW_A + TT_RAW_B;    // 14336 = 14 x 1024
@@ -83,7 +90,7 @@ constexpr size_t TT_SMEM = TT_BAR_OFF + (size_t)TT_NBAR * 8 + 16;
 static_assert(TT_RAW_STAGE % 1024 == 0 && TT_RAW_A % 1024 == 0, "swizzled TMA destinations");
 static_assert(TT_CONV_OFF % 1024 == 0 && TT_CSTAGE % 1024 == 0, "operand alignment");
 static_assert(TT_SMEM <= 227 * 1024, "one CTA per SM");
-static_assert(TT_NMAX * 4 <= TT_BITEMS * TT_CONV_THREADS, "B items per converter thread");
+static_assert(TT_NMAX * 4 <= TT_BITEMS * TT_GTHREADS, "B items per converter thread");
 // tensor-memory columns: accumulators, then the A slots (hi in 16 columns, lo in the next 16)
 constexpr uint32_t TT_TMEM_COLS = 512;
 constexpr uint32_t TT_ACC_STRIDE = 256;  // accumulator b at column 256 b
@@ -311,10 +318,10 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
   if (tid == 0) {
     for (int s = 0; s < TT_RS; ++s) {
       mbar_init(&raw_full[s], 1);
-      mbar_init(&raw_empty[s], TT_CONV_WARPS);
+      mbar_init(&raw_empty[s], TT_GWARPS);
     }
     for (int s = 0; s < TT_CS; ++s) {
-      mbar_init(&conv_full[s], TT_CONV_WARPS);
+      mbar_init(&conv_full[s], TT_GWARPS);
       mbar_init(&conv_empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -386,18 +393,20 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
     __syncwarp();
   } else if (warp < TT_CONV_WARPS) {
     // ------------------------------------------------------------ converters
-    const int q = warp & 3, kh = (warp >> 2) & 1;  // (kh: for the A warps 0-7)
+    const int grp = warp / TT_GWARPS, gw = warp % TT_GWARPS, gtid = tid % TT_GTHREADS;
+    const int q = warp & 3;               // tensor-memory lane quarter
+    const int kh0 = TT_KSPLIT == 2 ? gw >> 2 : 0;  // first half of the stage's k it converts
     const int l = 16 * q + (lane >> 1);  // complex row of the tile
     const int part = lane & 1;           // 0: (ar, -ai) -> Re rows; 1: (ai, ar) -> Im rows
     const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
-    // this thread's B items e = tid + 256 r: column n, pair j of complex k (2 j, 2 j + 1);
-    // packed n | j << 16 (-1: none), the raw-tile read index (op = N) and the offset in the
-    // split stage
+    // this thread's B items e = gtid + group size * r: column n, pair j of complex k (2 j,
+    // 2 j + 1); packed n | j << 16 (-1: none), the raw-tile read index (op = N) and the
+    // offset in the split stage
     int bitem[TT_BITEMS], brd[TT_BITEMS];
     uint32_t boff[TT_BITEMS];
 #pragma unroll
     for (int r = 0; r < TT_BITEMS; ++r) {
-      const int e = tid + TT_CONV_THREADS * r;
+      const int e = gtid + TT_GTHREADS * r;
       const int j = e / NB, n = e - j * NB;
       const bool v = e < 4 * NB;
       bitem[r] = v ? (n | (j << 16)) : -1;
@@ -411,6 +420,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
       bool v0, v1;
       const int nst = tile_stages(p, z, v0, v1);
       for (int st = 0; st < nst; ++st, ++it) {
+        if (it % TT_GROUPS != grp) continue;
         const bool g1 = !v0 || st >= p.seg[0].nkb;
         const bool ta = g1 ? TA1 : TA0, tb = g1 ? TB1 : TB0;
         const int s = it % TT_RS, cs = it % TT_CS;
@@ -425,8 +435,10 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
         }
         fence_after();
         const unsigned char* rs = sm_raw + (size_t)s * TT_RAW_STAGE;
-        if (warp < TT_AWARPS) {
-          // A: four complex k of row l
+        // A: four complex k of row l per half of the stage's k
+#pragma unroll
+        for (int hh = 0; hh < 3 - TT_KSPLIT; ++hh) {
+          const int kh = kh0 + hh;
           float2 a[4];
           if (!ta) {
 #pragma unroll
