@@ -1246,12 +1246,20 @@ cudaError_t gemm(int M, int N, int K, bool ta, bool tb, cplx<T> alpha, const cpl
   // small batches (the last reduction levels) leave most SMs idle with large tiles and
   // are latency-bound: use 32 x 32 output tiles there
   const int64_t big_tiles = (int64_t)batch * ceil_div(M, 80) * ceil_div(N, 80);
-  // FP32 products with enough tiles to fill the GPU run on the tensor cores (3xTF32)
+  // FP32 products run on the tensor cores (3xTF32): the TMA-fed kernel at any batch where it
+  // applies (its 64-row tiles keep even one product on several SMs, and a tile takes a few
+  // microseconds); the register-staged kernels where enough tiles fill the GPU
   if constexpr (sizeof(T) == 4) {
+    if (status && alpha.y == 0.f && beta.y == 0.f) {
+      const cudaError_t e = launch_tc_cgemm_tma(M, N, K, ta, tb, alpha.x, A, lda, sA, B, ldb, sB,
+                                                beta.x, C0, ldc0, sC0, C, ldc, sC, batch, status,
+                                                tc_wait_limit(), s);
+      if (e != cudaErrorNotSupported) return e;
+    }
     const int64_t tc_tiles = (int64_t)batch * ceil_div(M, 128) * ceil_div(N, 80);
     if (status && tc_tiles >= 152)
       return launch_tc_cgemm(M, N, K, ta, tb, alpha, A, lda, sA, B, ldb, sB, beta, C0, ldc0, sC0,
-                             C, ldc, sC, batch, status, s);
+                             C, ldc, sC, batch, status, s, 1);
   }
   if (big_tiles < 2 * 152) return gemm_tn<T, 2, 2>(a, ta, tb, batch, s);
   switch (pick_tile(M)) {
@@ -2086,7 +2094,7 @@ static cudaError_t factor_t(BcrHandle* h, const double2* dg, const double2* cx, 
     // batched products
     bool fused = false;
     if constexpr (sizeof(T) == 4) {
-      if (nk >= 2 && my >= 1 && (int64_t)nk * ceil_div(ny, 64) >= 152) {
+      if (nk >= 2 && my >= 1) {
         const TcSegment g[2] = {
             {L, ny, 2 * nn, nk, false, Y, ny, nn, my, false, ny, 0, -1, 1, nk},
             {L + nn, ny, 2 * nn, m, true, X, ny, nn, m, false, ny, 0, 0, 0, m}};
