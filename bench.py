@@ -143,9 +143,9 @@ def _replica_value(ws: int, steps: int, slowest_ms: float) -> float:
 
 # DRAM bytes (read + write) per ny x ny block inverted by the FP32 tensor-core Gauss-Jordan
 # kernel, from one ncu capture of its 1010-block launch in the 200-wavelength factorisation
-# (223.4 MB read + 154.6 MB written; algorithmic 409.6 KB per block).  Only valid for ny = 160
+# (225.6 MB read + 155.2 MB written; algorithmic 409.6 KB per block).  Only valid for ny = 160
 # and that kernel as it stands.
-GJ_TC_DRAM_BYTES_PER_BLOCK_NY160 = (223.432192e6 + 154.62784e6) / 1010
+GJ_TC_DRAM_BYTES_PER_BLOCK_NY160 = (225.58208e6 + 155.15264e6) / 1010
 # nominal dense TF32 / BF16 tensor rate (1.1 / 2.25 PFLOP/s)
 TF32_OVER_BF16 = 1.1 / 2.25
 
