@@ -1613,15 +1613,19 @@ __device__ __forceinline__ void rows_mv(const cplx<T>* __restrict__ M, const cpl
 // matrices' row vectors are loaded before any product, so a block streams its 2 x RC rows
 // in one memory phase (the sums are formed in the order of two rows_mv calls).
 template <typename T, int SMAX>
-__device__ __forceinline__ void rows_mv2(const cplx<T>* __restrict__ M1, const cplx<T>* x1,
-                                         const cplx<T>* __restrict__ M2, const cplx<T>* x2,
-                                         int ny, int r0, cplx<T>* out, const cplx<T>* sub) {
+struct Rows2 {  // this thread's 16-byte vectors of the RPW rows of two matrices
+  typename vec16<T>::type v1[RC / CH_WARPS][SMAX], v2[RC / CH_WARPS][SMAX];
+};
+
+// Issue the loads of rows r0 + warp + CH_WARPS i of M1 and M2 (no dependence on x).
+template <typename T, int SMAX>
+__device__ __forceinline__ void rows_load2(Rows2<T, SMAX>& R, const cplx<T>* __restrict__ M1,
+                                           const cplx<T>* __restrict__ M2, int ny, int r0) {
   using V = typename vec16<T>::type;
   constexpr int PER = vec16<T>::per;
   constexpr int RPW = RC / CH_WARPS;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nv = ny / PER;
-  V v1[RPW][SMAX], v2[RPW][SMAX];
 #pragma unroll
   for (int i = 0; i < RPW; ++i) {
     const int r = r0 + warp + CH_WARPS * i;
@@ -1631,11 +1635,23 @@ __device__ __forceinline__ void rows_mv2(const cplx<T>* __restrict__ M1, const c
     for (int s = 0; s < SMAX; ++s) {
       const int q = lane + 32 * s;
       if (r < ny && q < nv) {
-        v1[i][s] = __ldg(A + q);
-        v2[i][s] = __ldg(B + q);
+        R.v1[i][s] = __ldg(A + q);
+        R.v2[i][s] = __ldg(B + q);
       }
     }
   }
+}
+
+// out[r] = (sub[r] - M1[r] . x1) - M2[r] . x2 for the rows loaded by rows_load2 (x1, x2 in
+// shared memory).
+template <typename T, int SMAX>
+__device__ __forceinline__ void rows_dot2(const Rows2<T, SMAX>& R, const cplx<T>* x1,
+                                          const cplx<T>* x2, int ny, int r0, cplx<T>* out,
+                                          const cplx<T>* sub) {
+  constexpr int PER = vec16<T>::per;
+  constexpr int RPW = RC / CH_WARPS;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nv = ny / PER;
 #pragma unroll
   for (int i = 0; i < RPW; ++i) {
     const int r = r0 + warp + CH_WARPS * i;
@@ -1644,8 +1660,8 @@ __device__ __forceinline__ void rows_mv2(const cplx<T>* __restrict__ M1, const c
     for (int s = 0; s < SMAX; ++s) {
       const int q = lane + 32 * s;
       if (r < ny && q < nv) {
-        a1 = dot_vec<T>(v1[i][s], x1, PER * q, a1);
-        a2 = dot_vec<T>(v2[i][s], x2, PER * q, a2);
+        a1 = dot_vec<T>(R.v1[i][s], x1, PER * q, a1);
+        a2 = dot_vec<T>(R.v2[i][s], x2, PER * q, a2);
       }
     }
     a1 = warp_sum<T>(a1);
@@ -1771,6 +1787,17 @@ bwd_chunk_kernel(const cplx<T>* __restrict__ X, const cplx<T>* __restrict__ Y,
   const int c0 = blockIdx.y * RC;
   const int64_t nn = (int64_t)ny * ny;
   const bool has_b = 2 * k + 2 < n;
+  // x = (t - X xa) - Y xb on the chunk rows; X and Y rows streamed together where the
+  // register tiles of both fit (FP32 rows up to 192 columns), their loads issued before
+  // the vectors they multiply are read, else one after the other
+  // (early loads for rows up to 192 columns, where the register tiles keep two CTAs per SM)
+  constexpr bool fuse = sizeof(T) == 4 && SMAX <= 6;
+  constexpr bool early = fuse && SMAX <= 3;
+  const bool fused = fuse && has_b && k < m;
+  Rows2<T, fuse ? SMAX : 1> R;
+  if constexpr (early) {
+    if (fused) rows_load2<T, SMAX>(R, X + k * nn, Y + k * nn, ny, c0);
+  }
   for (int c = threadIdx.x; c < ny; c += CH_THREADS) {
     xa[c] = xup[k * ny + c];
     xb[c] = has_b ? xup[(k + 1) * ny + c] : czero<T>();
@@ -1779,11 +1806,11 @@ bwd_chunk_kernel(const cplx<T>* __restrict__ X, const cplx<T>* __restrict__ Y,
     xl[2 * k * ny + c] = xup[k * ny + c];
   __syncthreads();
   if (k >= m) return;
-  // x = (t - X xa) - Y xb on the chunk rows; X and Y rows streamed together where the
-  // register tiles of both fit (FP32 rows up to 192 columns), else one after the other
-  constexpr bool fuse = sizeof(T) == 4 && SMAX <= 6;
-  if (fuse && has_b) {
-    rows_mv2<T, SMAX>(X + k * nn, xa, Y + k * nn, xb, ny, c0, xl + (2 * k + 1) * ny, t + k * ny);
+  if (fused) {
+    if constexpr (fuse) {
+      if constexpr (!early) rows_load2<T, SMAX>(R, X + k * nn, Y + k * nn, ny, c0);
+      rows_dot2<T, SMAX>(R, xa, xb, ny, c0, xl + (2 * k + 1) * ny, t + k * ny);
+    }
   } else if (has_b) {
     rows_mv<T, SMAX>(X + k * nn, xa, ny, c0, tmp, t + k * ny);
     __syncthreads();
