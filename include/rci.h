@@ -138,6 +138,10 @@ typedef struct {
                             reduction level) over the largest among A's coefficients.  Block
                             cyclic reduction pivots only inside blocks, so large values flag a
                             factorisation whose rounding errors refinement must absorb. */
+  int32_t krylov_steps;  /* FP32_REFINE: preconditioned steps of the Krylov refinement taken
+                            after plain refinement stalled (0: plain refinement sufficed);
+                            they are included in refine_iters */
+  int32_t reserved;
 } rci_info;
 
 typedef struct rci_grid rci_grid;
@@ -176,9 +180,14 @@ rci_status rci_solve(rci_grid* g, const double* b, double* x, int64_t nrhs, rci_
 /* Iterative refinement settings of the grid: stop when ||b - A x||_2 / ||b||_2 <= tol
  * (FP64 stencil residual) or after max_steps corrections (the first FP32 solve is not
  * counted).  Defaults: FP32_REFINE tol 1e-10, 30 steps; FP64 tol 1e-13, 2 steps.
- * An FP32_REFINE grid whose refinement fails -- a non-finite residual, a step that
- * reduces the residual less than 0.7-fold (after the second), more than max_steps
- * steps, or a zero FP32 pivot in rci_factor -- factors the current design once in FP64
+ * When plain refinement of a single right-hand side stalls (a step that reduces the
+ * residual less than 0.7-fold, after the second, or max_steps steps), it continues with
+ * flexible GMRES on the FP64 stencil operator preconditioned by the FP32 factorisation
+ * (restarted every 16 steps; each step one FP32 solve, counted in the same max_steps
+ * budget; rci_info.krylov_steps).
+ * An FP32_REFINE grid whose refinement fails -- a non-finite residual, plain and Krylov
+ * refinement both stalled or out of steps, or a zero FP32 pivot in rci_factor -- factors
+ * the current design once in FP64
  * (the FP64 factor store is allocated the first time, from the grid's memory source)
  * and finishes this and every later solve of that design on it (rci_info.fallback).
  * A solve that ends above tol returns RCI_ENOCONV with its best value (FP64 and fallback

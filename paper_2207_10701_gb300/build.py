@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librci.so")
-SOURCES = ["assemble.cu", "rhs.cu", "qform.cu", "bcr.cu", "tc_gemm.cu", "tc_gemm_tma.cu", "tc_gj.cu", "grad.cu", "correlated.cu", "serve.cu", "peaks.cu", "capi.cu"]
+SOURCES = ["assemble.cu", "rhs.cu", "qform.cu", "bcr.cu", "tc_gemm.cu", "tc_gemm_tma.cu", "tc_gj.cu", "grad.cu", "correlated.cu", "serve.cu", "peaks.cu", "krylov.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

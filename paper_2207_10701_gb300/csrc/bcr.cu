@@ -1609,6 +1609,54 @@ __device__ __forceinline__ void rows_mv(const cplx<T>* __restrict__ M, const cpl
   }
 }
 
+// rows_mv split in two: the row loads (no dependence on x) and the products, so that a
+// block can issue its loads before it waits for the vector it multiplies.
+template <typename T, int SMAX>
+struct Rows1 {
+  typename vec16<T>::type v[RC / CH_WARPS][SMAX];
+};
+
+template <typename T, int SMAX>
+__device__ __forceinline__ void rows_load1(Rows1<T, SMAX>& R, const cplx<T>* __restrict__ M, int ny,
+                                           int r0) {
+  using V = typename vec16<T>::type;
+  constexpr int PER = vec16<T>::per;
+  constexpr int RPW = RC / CH_WARPS;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nv = ny / PER;
+#pragma unroll
+  for (int i = 0; i < RPW; ++i) {
+    const int r = r0 + warp + CH_WARPS * i;
+    const V* Mr = reinterpret_cast<const V*>(M + (int64_t)r * ny);
+#pragma unroll
+    for (int s = 0; s < SMAX; ++s) {
+      const int q = lane + 32 * s;
+      if (r < ny && q < nv) R.v[i][s] = __ldg(Mr + q);
+    }
+  }
+}
+
+template <typename T, int SMAX>
+__device__ __forceinline__ void rows_dot1(const Rows1<T, SMAX>& R, const cplx<T>* x, int ny, int r0,
+                                          cplx<T>* out) {
+  constexpr int PER = vec16<T>::per;
+  constexpr int RPW = RC / CH_WARPS;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nv = ny / PER;
+#pragma unroll
+  for (int i = 0; i < RPW; ++i) {
+    const int r = r0 + warp + CH_WARPS * i;
+    cplx<T> acc = czero<T>();
+#pragma unroll
+    for (int s = 0; s < SMAX; ++s) {
+      const int q = lane + 32 * s;
+      if (r < ny && q < nv) acc = dot_vec<T>(R.v[i][s], x, PER * q, acc);
+    }
+    acc = warp_sum<T>(acc);
+    if (lane == 0 && r < ny) out[r] = acc;
+  }
+}
+
 // out[r] = sub[r] - M1[r, :] x1 - M2[r, :] x2 for the RC rows r0 .. r0+RC-1: both
 // matrices' row vectors are loaded before any product, so a block streams its 2 x RC rows
 // in one memory phase (the sums are formed in the order of two rows_mv calls).
@@ -1764,9 +1812,14 @@ fwd_chunk_kernel(const cplx<T>* __restrict__ Dinv, const cplx<T>* __restrict__ X
   const int64_t k = blockIdx.x;
   const int c0 = blockIdx.y * RC;
   const int64_t nn = (int64_t)ny * ny;
+  // the Dinv rows of the chunk are loaded before b (rows up to 192 columns in FP32)
+  constexpr bool early = sizeof(T) == 4 && SMAX <= 3;
+  Rows1<T, early ? SMAX : 1> R;
+  if constexpr (early) rows_load1<T, SMAX>(R, Dinv + k * nn, ny, c0);
   for (int c = threadIdx.x; c < ny; c += CH_THREADS) bs[c] = B[(2 * k + 1) * ny + c];
   __syncthreads();
-  rows_mv<T, SMAX>(Dinv + k * nn, bs, ny, c0, t + k * ny, nullptr);
+  if constexpr (early) rows_dot1<T, SMAX>(R, bs, ny, c0, t + k * ny);
+  else rows_mv<T, SMAX>(Dinv + k * nn, bs, ny, c0, t + k * ny, nullptr);
   // X^T b and Y^T b on the chunk columns, both matrices streamed together
   cols_mvT2<T>(X + k * nn, 2 * k + 2 < n ? Y + k * nn : nullptr, bs, ny, c0, red, P + k * ny,
                Q + k * ny);

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <complex>
 #include <cstring>
 #include <new>
 #include <string>
@@ -59,6 +60,11 @@ struct rci_grid {
   int64_t corr64_n = 0;
   DevMem mem64;  // where the fallback's buffers came from (cudaMalloc when the grid's own
                  // memory source, e.g. a serving arena, had no room left for them)
+  // Krylov refinement (allocated the first time plain refinement stalls): basis V
+  // (KR_M + 1 vectors), preconditioned directions Z (KR_M), a zero vector, dot scratch
+  double2* kbuf = nullptr;
+  double2* kpart = nullptr;
+  DevMem memk;
   // correlated-light inputs (theta, weights, C, alpha) and multi-output results (grown on demand)
   void* cbuf = nullptr;
   size_t cbuf_bytes = 0;
@@ -429,6 +435,157 @@ rci_status ensure_corr64(rci_grid* g, int64_t n) {
   return RCI_OK;
 }
 
+// Krylov refinement of one right-hand side: flexible GMRES on the FP64 stencil operator A,
+// right-preconditioned by the FP32 factorisation (z = M^-1 v by one FP32 solve; flexible,
+// since the FP32 solve is linear only up to rounding), restarted every KR_M steps, Gram-
+// Schmidt applied twice per step.  Used when plain refinement stalls: the Krylov space
+// corrects the few error directions the FP32 factorisation resolves poorly, at one FP32
+// solve per step, where the alternative is an FP64 factorisation.  Starts from x, takes at
+// most max_steps preconditioned steps; *worst is the true residual ratio at the end.
+constexpr int KR_M = 16;
+static_assert(KR_M + 1 <= KV_MAX_VECTORS, "basis fits one multi-dot");
+
+rci_status ensure_krylov(rci_grid* g) {
+  if (g->kbuf) return RCI_OK;
+  const size_t nvec = (size_t)(2 * KR_M + 2);  // V (KR_M + 1), Z (KR_M), zero
+  const size_t bytes = nvec * (size_t)g->N * sizeof(double2);
+  const size_t pbytes = ((size_t)KV_DOT_BLOCKS * KV_MAX_VECTORS + KV_MAX_VECTORS) * sizeof(double2);
+  g->memk = g->mem;
+  cudaError_t e = g->memk.alloc((void**)&g->kbuf, bytes);
+  if (e == cudaSuccess) e = g->memk.alloc((void**)&g->kpart, pbytes);
+  if (e == cudaErrorMemoryAllocation && g->mem.alloc_fn) {  // arena full: cudaMalloc
+    (void)cudaGetLastError();
+    g->memk.release(g->kbuf);
+    g->memk.release(g->kpart);
+    g->kbuf = g->kpart = nullptr;
+    g->memk = DevMem{};
+    e = g->memk.alloc((void**)&g->kbuf, bytes);
+    if (e == cudaSuccess) e = g->memk.alloc((void**)&g->kpart, pbytes);
+  }
+  if (e != cudaSuccess) {
+    g->memk.release(g->kbuf);
+    g->memk.release(g->kpart);
+    g->kbuf = g->kpart = nullptr;
+  }
+  CK(e, "Krylov refinement buffers");
+  double2* zero = g->kbuf + (size_t)(2 * KR_M + 1) * g->N;
+  CK(cudaMemsetAsync(zero, 0, sizeof(double2) * g->N, g->s), "Krylov zero vector");
+  return RCI_OK;
+}
+
+rci_status krylov_refine(rci_grid* g, const double2* b, double2* x, double2* r, void* a32,
+                         void* b32, int max_steps, int* steps, double* worst) {
+  using cd = std::complex<double>;
+  rci_status st = ensure_krylov(g);
+  if (st != RCI_OK) return st;
+  const int64_t N = g->N;
+  double2* V = g->kbuf;
+  double2* Z = V + (size_t)(KR_M + 1) * N;
+  double2* zero = Z + (size_t)KR_M * N;
+  double2* part = g->kpart;
+  double2* hdev = g->kpart + (size_t)KV_DOT_BLOCKS * KV_MAX_VECTORS;
+  // out[i] = (V_i, w) for i < nv, read back to the host
+  auto dots = [&](const double2* Vb, int nv, const double2* w, std::vector<cd>& out) -> rci_status {
+    std::vector<double2> h(nv);
+    CK(launch_cdot_multi(Vb, N, nv, w, N, part, hdev, g->s), "Krylov inner products");
+    CK(cudaMemcpyAsync(h.data(), hdev, sizeof(double2) * nv, cudaMemcpyDeviceToHost, g->s),
+       "Krylov inner products");
+    CK(cudaStreamSynchronize(g->s), "Krylov inner products");
+    out.assign(nv, cd());
+    for (int i = 0; i < nv; ++i) out[i] = cd(h[i].x, h[i].y);
+    return RCI_OK;
+  };
+  // w += sign sum_i c[i] V_i
+  auto combine = [&](double2* w, const double2* Vb, const std::vector<cd>& c, int nv,
+                     double sign) -> rci_status {
+    std::vector<double2> h(nv);
+    for (int i = 0; i < nv; ++i) h[i] = make_double2(c[i].real(), c[i].imag());
+    CK(cudaMemcpyAsync(hdev, h.data(), sizeof(double2) * nv, cudaMemcpyHostToDevice, g->s),
+       "Krylov coefficients");
+    CK(launch_caxpy_multi(w, Vb, N, nv, hdev, sign, N, g->s), "Krylov combination");
+    return RCI_OK;
+  };
+  std::vector<cd> t1;
+  if ((st = dots(b, 1, b, t1)) != RCI_OK) return st;
+  const double bnorm = std::sqrt(std::max(t1[0].real(), 0.0));
+  if (!(bnorm > 0.0)) return residual_ratio(g, b, x, r, 1, worst);
+  int used = 0;
+  double prev = 0.0;
+  for (int restart = 0; used < max_steps; ++restart) {
+    if ((st = residual_ratio(g, b, x, r, 1, worst)) != RCI_OK) return st;
+    if (*worst <= g->tol32) break;
+    if (restart > 0 && *worst > 0.5 * prev) break;  // a cycle that barely helps: give up
+    prev = *worst;
+    const double beta = *worst * bnorm;
+    CK(launch_cscale(V, r, 1.0 / beta, N, g->s), "Krylov basis");
+    std::vector<cd> H((size_t)(KR_M + 1) * KR_M, cd()), gv(KR_M + 1, cd()), sn(KR_M, cd());
+    std::vector<double> cs(KR_M, 0.0);
+    auto Hij = [&](int i, int j) -> cd& { return H[(size_t)i * KR_M + j]; };
+    gv[0] = beta;
+    int k = 0;
+    for (int j = 0; j < KR_M && used < max_steps; ++j) {
+      double2* vj = V + (size_t)j * N;
+      double2* zj = Z + (size_t)j * N;
+      double2* w = V + (size_t)(j + 1) * N;
+      // z_j = M^-1 v_j (one FP32 solve), w = A z_j (FP64 stencil: r = 0 - A z_j)
+      CK(launch_to_f32(vj, (float2*)a32, N, g->s), "Krylov to fp32");
+      CK(bcr_solve(g->bcr, g->cx, a32, b32, 1, g->s), "Krylov preconditioner");
+      CK(launch_to_f64((const float2*)b32, zj, N, g->s), "Krylov to fp64");
+      ++used;
+      CK(launch_residual(g->g, g->dg, g->cx, g->cy, zero, zj, r, 1, g->part_r, g->part_b, g->s),
+         "Krylov operator");
+      CK(launch_cscale(w, r, -1.0, N, g->s), "Krylov operator");
+      // w -= V h, twice (classical Gram-Schmidt with one reorthogonalisation)
+      std::vector<cd> h1, h2, nw;
+      if ((st = dots(V, j + 1, w, h1)) != RCI_OK) return st;
+      if ((st = combine(w, V, h1, j + 1, -1.0)) != RCI_OK) return st;
+      if ((st = dots(V, j + 1, w, h2)) != RCI_OK) return st;
+      if ((st = combine(w, V, h2, j + 1, -1.0)) != RCI_OK) return st;
+      if ((st = dots(w, 1, w, nw)) != RCI_OK) return st;
+      const double hn = std::sqrt(std::max(nw[0].real(), 0.0));
+      if (!std::isfinite(hn)) return fail(g, RCI_ENUMERIC, "non-finite Krylov step");
+      for (int i = 0; i <= j; ++i) Hij(i, j) = h1[i] + h2[i];
+      Hij(j + 1, j) = hn;
+      // earlier Givens rotations on the new column, then the one that zeroes H(j+1, j)
+      for (int i = 0; i < j; ++i) {
+        const cd a = Hij(i, j), c = Hij(i + 1, j);
+        Hij(i, j) = cs[i] * a + sn[i] * c;
+        Hij(i + 1, j) = -std::conj(sn[i]) * a + cs[i] * c;
+      }
+      {
+        const cd a = Hij(j, j), c = Hij(j + 1, j);
+        const double nu = std::sqrt(std::norm(a) + std::norm(c));
+        if (std::abs(a) == 0.0) {
+          cs[j] = 0.0;
+          sn[j] = 1.0;
+          Hij(j, j) = c;
+        } else {
+          const cd ph = a / std::abs(a);
+          cs[j] = std::abs(a) / nu;
+          sn[j] = ph * std::conj(c) / nu;
+          Hij(j, j) = ph * nu;
+        }
+        Hij(j + 1, j) = 0.0;
+        gv[j + 1] = -std::conj(sn[j]) * gv[j];
+        gv[j] = cs[j] * gv[j];
+      }
+      k = j + 1;
+      if (hn > 0.0) CK(launch_cscale(w, w, 1.0 / hn, N, g->s), "Krylov basis");
+      if (std::abs(gv[j + 1]) <= 0.5 * g->tol32 * bnorm || hn == 0.0) break;
+    }
+    // x += Z y with R y = g (R: the rotated Hessenberg matrix)
+    std::vector<cd> y(k, cd());
+    for (int i = k - 1; i >= 0; --i) {
+      cd t = gv[i];
+      for (int l = i + 1; l < k; ++l) t -= Hij(i, l) * y[l];
+      y[i] = Hij(i, i) != 0.0 ? t / Hij(i, i) : cd();
+    }
+    if (k > 0 && (st = combine(x, Z, y, k, 1.0)) != RCI_OK) return st;
+  }
+  *steps = used;
+  return residual_ratio(g, b, x, r, 1, worst);
+}
+
 // Solve A x = b (FP64 in/out, device, nrhs columns) with the grid's factorisation and
 // iterative refinement on the FP64 stencil residual.  r, a32, b32 are scratch buffers of
 // the same length: complex64 for FP32 grids; for FP64 grids a32 is complex128 (the
@@ -439,7 +596,7 @@ rci_status refined_solve(rci_grid* g, const double2* b, double2* x, double2* r, 
                          void* b32, int nrhs, rci_info* info) {
   const int64_t n = g->N * nrhs;
   double worst = 0.0;
-  int it = 0;
+  int it = 0, kry = 0;
   bool fell_back = false;
   rci_status st = RCI_OK;
   if (g->d.prec == RCI_FP64) {
@@ -464,6 +621,16 @@ rci_status refined_solve(rci_grid* g, const double2* b, double2* x, double2* r, 
         if (st != RCI_OK) return st;
         if (worst <= g->tol32) break;
         if (it >= g->max_refine32 || (it >= 3 && worst > 0.7 * prev)) {
+          // plain refinement stalled: one right-hand side continues with the Krylov
+          // refinement within the remaining step budget before the FP64 fallback
+          if (nrhs == 1 && it < g->max_refine32) {
+            int ks = 0;
+            st = krylov_refine(g, b, x, r, a32, b32, g->max_refine32 - it, &ks, &worst);
+            it += ks;
+            kry = ks;
+            if (st == RCI_OK && worst <= g->tol32) break;
+            if (st != RCI_OK && st != RCI_ENUMERIC) return st;
+          }
           need64 = true;
           break;
         }
@@ -487,6 +654,7 @@ rci_status refined_solve(rci_grid* g, const double2* b, double2* x, double2* r, 
     info->rel_residual = worst;
     info->fallback = fell_back ? 1 : 0;
     info->growth_est = fell_back ? g->growth64 : g->growth;
+    info->krylov_steps = kry;
   }
   if (nrhs > 1) {  // the multi-RHS solve runs tensor-core GEMMs with bounded waits
     int32_t dst = 0;
@@ -614,6 +782,8 @@ void destroy_grid(rci_grid* g, bool sync) {
                 g->tabbuf};
   for (void* p : ps) dfree(g, p);
   g->mem64.release(g->corr64);
+  g->memk.release(g->kbuf);
+  g->memk.release(g->kpart);
   bcr_destroy(g->bcr);
   bcr_destroy(g->bcr64);
   if (g->prof.pool) {
@@ -1002,6 +1172,7 @@ rci_status rci_avg_intensity_grad(rci_grid* g, const rci_objective* obj, const r
     info->rel_residual = i1.rel_residual > i2.rel_residual ? i1.rel_residual : i2.rel_residual;
     info->fallback = i1.fallback | i2.fallback;
     info->growth_est = i2.growth_est > i1.growth_est ? i2.growth_est : i1.growth_est;
+    info->krylov_steps = i1.krylov_steps + i2.krylov_steps;
     float ms = 0;
     cudaEventElapsedTime(&ms, g->ev[2], g->ev[3]);
     info->ms_solve = i1.ms_solve + ms;

@@ -37,6 +37,19 @@ cudaError_t launch_to_f64(const float2* a, double2* out, int64_t n, cudaStream_t
 cudaError_t launch_axpy64(double2* x, const double2* d, int64_t n, cudaStream_t s);
 cudaError_t launch_check_finite(const double2* a, int64_t n, int32_t* status, cudaStream_t s);
 
+// krylov.cu: FP64 complex vectors of n elements, nv <= KV_MAX_VECTORS vectors V_i at V + i ldv.
+constexpr int KV_MAX_VECTORS = 20;
+constexpr int KV_DOT_BLOCKS = 4 * 152;  // blocks of the multi-dot (part holds
+                                        // KV_DOT_BLOCKS x KV_MAX_VECTORS entries)
+// out[i] = sum_e conj(V_i[e]) w[e]  (device out[nv]; part: device scratch)
+cudaError_t launch_cdot_multi(const double2* V, int64_t ldv, int nv, const double2* w, int64_t n,
+                              double2* part, double2* out, cudaStream_t s);
+// w += sign sum_i coef[i] V_i  (coef: device, nv entries)
+cudaError_t launch_caxpy_multi(double2* w, const double2* V, int64_t ldv, int nv,
+                               const double2* coef, double sign, int64_t n, cudaStream_t s);
+// out = f in (out may be in)
+cudaError_t launch_cscale(double2* out, const double2* in, double f, int64_t n, cudaStream_t s);
+
 // rhs.cu
 cudaError_t launch_gauss_legendre(int n, double a, double b, double* nodes, double* weights,
                                   cudaStream_t s);

@@ -45,7 +45,8 @@ class InfoC(C.Structure):
     _fields_ = [("refine_iters", C.c_int32), ("fallback", C.c_int32),
                 ("rel_residual", C.c_double), ("ms_factor", C.c_double),
                 ("ms_solve", C.c_double), ("ms_qform", C.c_double),
-                ("growth_est", C.c_double)]
+                ("growth_est", C.c_double), ("krylov_steps", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class ServerDescC(C.Structure):
@@ -99,11 +100,12 @@ class Info:
     ms_qform: float
     fallback: bool = False
     growth_est: float = 0.0
+    krylov_steps: int = 0
 
     @staticmethod
     def of(c: InfoC) -> "Info":
         return Info(c.refine_iters, c.rel_residual, c.ms_factor, c.ms_solve, c.ms_qform,
-                    bool(c.fallback), c.growth_est)
+                    bool(c.fallback), c.growth_est, c.krylov_steps)
 
 
 class RciError(RuntimeError):
