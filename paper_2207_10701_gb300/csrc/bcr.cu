@@ -2165,38 +2165,75 @@ static cudaError_t factor_t(BcrHandle* h, const double2* dg, const double2* cx, 
       RCI_CUDA_TRY(launch_gj<T>(D + nn, 2 * nn, Dinv, nn, ny, m, h->status, s, maxabs + 1));
     }
     // X_k = Dinv_k L_{2k+1};  Y_k = Dinv_k L_{2k+2}^T
-    RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, false, one, Dinv, ny, nn, L + nn, ny, 2 * nn, zero,
-                         nullptr, 0, 0, X, ny, nn, m, s, h->prof, PF_GEMM, h->status));
-    RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, true, one, Dinv, ny, nn, L + 2 * nn, ny, 2 * nn, zero,
-                         nullptr, 0, 0, Y, ny, nn, my, s, h->prof, PF_GEMM, h->status));
-    // D'_k = D_{2k} - L_{2k} Y_{k-1} (k >= 1) - L_{2k+1}^T X_k (k < m): on the tensor cores one
-    // product over K = 2 ny per kept row (D' written once); otherwise a copy of D_0 and two
-    // batched products
+    // D'_k = D_{2k} - L_{2k} Y_{k-1} (k >= 1) - L_{2k+1}^T X_k (k < m)
+    // L'_k = -L_{2k} X_{k-1} (k >= 1)
+    // FP32 on the tensor cores: two launches, X and Y together, then each D' as one product
+    // over K = 2 ny (written once) together with L'; otherwise five batched products.
     bool fused = false;
     if constexpr (sizeof(T) == 4) {
       if (nk >= 2 && my >= 1) {
-        const TcSegment g[2] = {
-            {L, ny, 2 * nn, nk, false, Y, ny, nn, my, false, ny, 0, -1, 1, nk},
-            {L + nn, ny, 2 * nn, m, true, X, ny, nn, m, false, ny, 0, 0, 0, m}};
-        ProfScope ps(h->prof, PF_GEMM, s, 8.0 * ny * (double)nn * (nk - 1 + m),
-                     (double)sizeof(cplx<T>) * nn * (2.0 * (nk - 1 + m) + 2.0 * nk), 1);
-        const cudaError_t e = launch_tc_cgemm_tma_seg(ny, ny, 2, g, -1.f, 1.f, D, ny, 2 * nn, Dn, ny,
-                                                      nn, nk, h->status, tc_wait_limit(), s);
-        if (e == cudaSuccess) fused = true;
-        else if (e != cudaErrorNotSupported) return e;
+        const double pb = (double)sizeof(cplx<T>) * nn;
+        TcJob xy[2] = {};
+        xy[0].nseg = 1;
+        xy[0].seg[0] = TcSegment{Dinv, ny, nn, m, false, L + nn, ny, 2 * nn, m, false, ny, 0, 0, 0, m};
+        xy[0].alpha = 1.f;
+        xy[0].C = X;
+        xy[0].ldc = ny;
+        xy[0].sC = nn;
+        xy[0].batch = m;
+        xy[1] = xy[0];
+        xy[1].seg[0] = TcSegment{Dinv, ny, nn, my, false, L + 2 * nn, ny, 2 * nn, my, true, ny, 0, 0, 0, my};
+        xy[1].C = Y;
+        xy[1].batch = my;
+        TcJob sl[2] = {};
+        sl[0].nseg = 2;
+        sl[0].seg[0] = TcSegment{L, ny, 2 * nn, nk, false, Y, ny, nn, my, false, ny, 0, -1, 1, nk};
+        sl[0].seg[1] = TcSegment{L + nn, ny, 2 * nn, m, true, X, ny, nn, m, false, ny, 0, 0, 0, m};
+        sl[0].alpha = -1.f;
+        sl[0].beta = 1.f;
+        sl[0].C0 = D;
+        sl[0].ldc0 = ny;
+        sl[0].sC0 = 2 * nn;
+        sl[0].C = Dn;
+        sl[0].ldc = ny;
+        sl[0].sC = nn;
+        sl[0].batch = nk;
+        sl[1].nseg = 1;
+        sl[1].seg[0] = TcSegment{L + 2 * nn, ny, 2 * nn, nk - 1, false, X, ny, nn, m, false, ny, 0, 0, 0, nk - 1};
+        sl[1].alpha = -1.f;
+        sl[1].C = Ln + nn;
+        sl[1].ldc = ny;
+        sl[1].sC = nn;
+        sl[1].batch = nk - 1;
+        cudaError_t e;
+        {
+          ProfScope ps(h->prof, PF_GEMM, s, 8.0 * ny * (double)nn * (m + my), pb * 3.0 * (m + my), 1);
+          e = launch_tc_cgemm_tma_jobs(ny, ny, 2, xy, h->status, tc_wait_limit(), s);
+        }
+        if (e == cudaSuccess) {
+          ProfScope ps(h->prof, PF_GEMM, s, 8.0 * ny * (double)nn * (2 * (nk - 1) + m),
+                       pb * (2.0 * (nk - 1 + m) + 2.0 * nk + 3.0 * (nk - 1)), 1);
+          RCI_CUDA_TRY(launch_tc_cgemm_tma_jobs(ny, ny, 2, sl, h->status, tc_wait_limit(), s));
+          fused = true;
+        } else if (e != cudaErrorNotSupported) {
+          return e;
+        }
       }
     }
     if (!fused) {
+      RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, false, one, Dinv, ny, nn, L + nn, ny, 2 * nn, zero,
+                           nullptr, 0, 0, X, ny, nn, m, s, h->prof, PF_GEMM, h->status));
+      RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, true, one, Dinv, ny, nn, L + 2 * nn, ny, 2 * nn, zero,
+                           nullptr, 0, 0, Y, ny, nn, my, s, h->prof, PF_GEMM, h->status));
       RCI_CUDA_TRY(cudaMemcpyAsync(Dn, D, nn * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s));
       RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, false, mone, L + 2 * nn, ny, 2 * nn, Y, ny, nn, one,
                            D + 2 * nn, ny, 2 * nn, Dn + nn, ny, nn, nk - 1, s, h->prof, PF_GEMM,
                            h->status));
       RCI_CUDA_TRY(gemm<T>(ny, ny, ny, true, false, mone, L + nn, ny, 2 * nn, X, ny, nn, one, Dn,
                            ny, nn, Dn, ny, nn, m, s, h->prof, PF_GEMM, h->status));
+      RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, false, mone, L + 2 * nn, ny, 2 * nn, X, ny, nn, zero,
+                           nullptr, 0, 0, Ln + nn, ny, nn, nk - 1, s, h->prof, PF_GEMM, h->status));
     }
-    // L'_k = -L_{2k} X_{k-1} (k >= 1)
-    RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, false, mone, L + 2 * nn, ny, 2 * nn, X, ny, nn, zero,
-                         nullptr, 0, 0, Ln + nn, ny, nn, nk - 1, s, h->prof, PF_GEMM, h->status));
     cur = 1 - cur;
   }
   // last single row

@@ -38,13 +38,31 @@ struct TcSegment {
   int zA, zB, zlo, zhi;
 };
 
-// C[z] = alpha sum_g op(A_g[z + zA_g]) op(B_g[z + zB_g]) + beta C0[z] over the segments that
-// include z (one, or two with (op A, op B) = (N, N) then (T, N)); same shape and alignment
-// rules as launch_tc_cgemm_tma, cudaErrorNotSupported (nothing launched) otherwise.
+// C[z] = alpha sum_g op(A_g[z + zA_g]) op(B_g[z + zB_g]) + beta C0[z] over the segments (one
+// or two, each with its own transposes) that include z; same shape and alignment rules as
+// launch_tc_cgemm_tma, cudaErrorNotSupported (nothing launched) otherwise.
 cudaError_t launch_tc_cgemm_tma_seg(int M, int N, int nseg, const TcSegment* seg, float alpha,
                                     float beta, const float2* C0, int64_t ldc0, int64_t sC0,
                                     float2* C, int64_t ldc, int64_t sC, int batch, int32_t* status,
                                     long long wait_limit, cudaStream_t s);
+
+// One set of products of a TMA-fed launch: C[z] (z < batch) as in launch_tc_cgemm_tma_seg.
+struct TcJob {
+  int nseg;
+  TcSegment seg[2];
+  float alpha, beta;
+  const float2* C0;
+  int64_t ldc0, sC0;
+  float2* C;
+  int64_t ldc, sC;
+  int batch;
+};
+
+// One launch over up to two jobs with the same M and N (their tiles numbered job after job);
+// a job with batch 0 is skipped.  cudaErrorNotSupported (nothing launched) where any job's
+// operands break the TMA rules.
+cudaError_t launch_tc_cgemm_tma_jobs(int M, int N, int njob, const TcJob* jobs, int32_t* status,
+                                     long long wait_limit, cudaStream_t s);
 
 // Cycles a pipeline wait inside the tensor-core kernels may spin before the kernel gives
 // up with DEV_TIMEOUT (process-wide; <= 0 restores the default of 4e9 cycles, ~2 s).  The

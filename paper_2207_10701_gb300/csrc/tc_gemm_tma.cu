@@ -100,33 +100,76 @@ __device__ __forceinline__ uint32_t a_slot(int cs) {
 static_assert(TT_CS <= 6, "six A slots fit beside the accumulators");
 constexpr long long TT_DEFAULT_WAIT = 4000000000LL;
 
-// A product may run over up to two K segments with their own operands (the Schur update
-// D - L_2k Y_k-1 - L_2k+1^T X_k as one product over K = 2 ny): segment g of output z reads A
-// member z + zA and B member z + zB of its tensor maps, for zlo <= z < zhi only.
+// A launch runs up to two jobs (independent sets of products with their own operands and
+// outputs, e.g. X = Dinv L and Y = Dinv L^T of one reduction level), their tiles numbered job
+// after job.  A product may run over up to two K segments with their own operands (the Schur
+// update D - L_2k Y_k-1 - L_2k+1^T X_k as one product over K = 2 ny): segment g of output z
+// reads A member z + zA and B member z + zB of its tensor maps, for zlo <= z < zhi only.
 struct TtSeg {
   int nkb;          // K stages (8 complex k each)
   int zA, zB;       // batch offsets of its operands
   int zlo, zhi;     // outputs that include this segment
+  int ta, tb;       // op(A), op(B): 1 = transpose
 };
 
-struct TtArgs {
-  int M, N, NB;     // NB: N rounded up to 16 (the MMA's N)
-  int batch, nseg;
+struct TtJob {
+  int batch, nseg, tile0;  // tile0: the job's first tile in the launch
   TtSeg seg[2];
   float2* C;
   int64_t ldc, sC;
   const float2* C0;
   int64_t ldc0, sC0;
   float alpha, beta;
+};
+
+struct TtArgs {
+  int M, N, NB;     // NB: N rounded up to 16 (the MMA's N)
+  int njob, ntiles;
+  TtJob job[2];
   int32_t* status;
   long long wait_limit;
 };
 
-// stages of output z and whether each segment takes part
-__device__ __forceinline__ int tile_stages(const TtArgs& p, int z, bool& v0, bool& v1) {
-  v0 = z >= p.seg[0].zlo && z < p.seg[0].zhi;
-  v1 = p.nseg > 1 && z >= p.seg[1].zlo && z < p.seg[1].zhi;
-  return (v0 ? p.seg[0].nkb : 0) + (v1 ? p.seg[1].nkb : 0);
+// tensor maps: job j, segment g: A at 4 j + 2 g, B at 4 j + 2 g + 1
+struct TtMaps {
+  CUtensorMap m[8];
+};
+
+// the address of map i, each one a constant offset into the parameter
+__device__ __forceinline__ const CUtensorMap* map_at(const TtMaps& maps, int i) {
+  switch (i) {
+    case 0: return &maps.m[0];
+    case 1: return &maps.m[1];
+    case 2: return &maps.m[2];
+    case 3: return &maps.m[3];
+    case 4: return &maps.m[4];
+    case 5: return &maps.m[5];
+    case 6: return &maps.m[6];
+    default: return &maps.m[7];
+  }
+}
+
+struct TtTile {
+  int j, z, i0;     // job, product within the job, first row
+};
+
+// (jobs: the launch's jobs copied to shared memory: reading the job of a tile straight from
+// the kernel parameter at a run-time index gave wrong rows in the library build, and the
+// tensor maps are taken at constant offsets for the same reason)
+__device__ __forceinline__ TtTile tile_of(const TtJob* jobs, int njob, int tile, int mt) {
+  TtTile t;
+  t.j = (njob > 1 && tile >= jobs[1].tile0) ? 1 : 0;
+  const int local = tile - jobs[t.j].tile0;
+  t.z = local / mt;
+  t.i0 = (local - t.z * mt) * TT_ROWS;
+  return t;
+}
+
+// stages of output z of a job and whether each segment takes part
+__device__ __forceinline__ int tile_stages(const TtJob& q, int z, bool& v0, bool& v1) {
+  v0 = z >= q.seg[0].zlo && z < q.seg[0].zhi;
+  v1 = q.nseg > 1 && z >= q.seg[1].zlo && z < q.seg[1].zhi;
+  return (v0 ? q.seg[0].nkb : 0) + (v1 ? q.seg[1].nkb : 0);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -285,12 +328,8 @@ __device__ __forceinline__ void fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-template <bool TA0, bool TB0, bool TA1, bool TB1>
 __global__ void __launch_bounds__(TT_THREADS, 1)
-    tc_cgemm_tma_kernel(const __grid_constant__ CUtensorMap tmA0,
-                        const __grid_constant__ CUtensorMap tmB0,
-                        const __grid_constant__ CUtensorMap tmA1,
-                        const __grid_constant__ CUtensorMap tmB1, TtArgs p) {
+    tc_cgemm_tma_kernel(const __grid_constant__ TtMaps maps, const __grid_constant__ TtArgs p) {
   extern __shared__ __align__(1024) unsigned char sm_raw[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm_raw + TT_BAR_OFF);
   uint64_t* raw_full = bars;
@@ -305,7 +344,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int mt = (p.M + TT_ROWS - 1) / TT_ROWS;               // row tiles per product
-  const int64_t ntiles = (int64_t)mt * p.batch;
+  const int64_t ntiles = p.ntiles;
   const int ntl = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
   const int NB = p.NB;
   // the swizzled TMA destinations assume a 1024-byte aligned shared-memory window: refuse to
@@ -315,7 +354,10 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
     return;
   }
 
+  __shared__ TtJob jobs[2];
   if (tid == 0) {
+    jobs[0] = p.job[0];
+    jobs[1] = p.job[1];
     for (int s = 0; s < TT_RS; ++s) {
       mbar_init(&raw_full[s], 1);
       mbar_init(&raw_empty[s], TT_GWARPS);
@@ -352,11 +394,10 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
       int it = 0;
       bool ok = true;
       for (int tl = 0; tl < ntl && ok; ++tl) {
-        const int tile = (int)blockIdx.x + tl * (int)gridDim.x;
-        const int z = tile / mt;
-        const int i0 = (tile - z * mt) * TT_ROWS;
+        const TtTile t = tile_of(jobs, p.njob, (int)blockIdx.x + tl * (int)gridDim.x, mt);
+        const TtJob& q = jobs[t.j];
         bool v0, v1;
-        const int nst = tile_stages(p, z, v0, v1);
+        const int nst = tile_stages(q, t.z, v0, v1);
         for (int st = 0; st < nst; ++st, ++it) {
           const int s = it % TT_RS;
           if (it >= TT_RS &&
@@ -365,24 +406,19 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
             break;
           }
           if (lane != 0) continue;
-          const bool g1 = !v0 || st >= p.seg[0].nkb;
-          const int k0 = (g1 ? (v0 ? st - p.seg[0].nkb : st) : st) * TT_KC;
+          const int g = (!v0 || st >= q.seg[0].nkb) ? 1 : 0;
+          const TtSeg& sg = q.seg[g];
+          const int k0 = (g ? (v0 ? st - q.seg[0].nkb : st) : st) * TT_KC;
           unsigned char* rs = sm_raw + (size_t)s * TT_RAW_STAGE;
           const uint32_t ra = smem_u32(rs), rb = smem_u32(rs + TT_RAW_A);
+          const CUtensorMap* mA = map_at(maps, 4 * t.j + 2 * g);
+          const CUtensorMap* mB = map_at(maps, 4 * t.j + 2 * g + 1);
+          const int za = t.z + sg.zA, zb = t.z + sg.zB;
           mbar_expect_tx(&raw_full[s], bytes);
-          if (!g1) {
-            const int za = z + p.seg[0].zA, zb = z + p.seg[0].zB;
-            if (!TA0) tma_load_3d(ra, &tmA0, k0, i0, za, &raw_full[s]);
-            else tma_load_3d(ra, &tmA0, i0, k0, za, &raw_full[s]);
-            if (!TB0) tma_load_3d(rb, &tmB0, 0, k0, zb, &raw_full[s]);
-            else tma_load_3d(rb, &tmB0, k0, 0, zb, &raw_full[s]);
-          } else {
-            const int za = z + p.seg[1].zA, zb = z + p.seg[1].zB;
-            if (!TA1) tma_load_3d(ra, &tmA1, k0, i0, za, &raw_full[s]);
-            else tma_load_3d(ra, &tmA1, i0, k0, za, &raw_full[s]);
-            if (!TB1) tma_load_3d(rb, &tmB1, 0, k0, zb, &raw_full[s]);
-            else tma_load_3d(rb, &tmB1, k0, 0, zb, &raw_full[s]);
-          }
+          if (!sg.ta) tma_load_3d(ra, mA, k0, t.i0, za, &raw_full[s]);
+          else tma_load_3d(ra, mA, t.i0, k0, za, &raw_full[s]);
+          if (!sg.tb) tma_load_3d(rb, mB, 0, k0, zb, &raw_full[s]);
+          else tma_load_3d(rb, mB, k0, 0, zb, &raw_full[s]);
         }
       }
       // the copies lane 0 issued land before the CTA can exit
@@ -416,13 +452,14 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
     int it = 0;
     bool ok = true;
     for (int tl = 0; tl < ntl && ok; ++tl) {
-      const int z = ((int)blockIdx.x + tl * (int)gridDim.x) / mt;
+      const TtTile t = tile_of(jobs, p.njob, (int)blockIdx.x + tl * (int)gridDim.x, mt);
+      const TtJob& q = jobs[t.j];
       bool v0, v1;
-      const int nst = tile_stages(p, z, v0, v1);
+      const int nst = tile_stages(q, t.z, v0, v1);
       for (int st = 0; st < nst; ++st, ++it) {
         if (it % TT_GROUPS != grp) continue;
-        const bool g1 = !v0 || st >= p.seg[0].nkb;
-        const bool ta = g1 ? TA1 : TA0, tb = g1 ? TB1 : TB0;
+        const int g = (!v0 || st >= q.seg[0].nkb) ? 1 : 0;
+        const bool ta = q.seg[g].ta != 0, tb = q.seg[g].tb != 0;
         const int s = it % TT_RS, cs = it % TT_CS;
         if (!warp_wait(&raw_full[s], (uint32_t)((it / TT_RS) & 1), abort_flag, p.wait_limit)) {
           ok = false;
@@ -515,9 +552,9 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
         break;
       fence_after();
       const uint32_t acc = tmem + (uint32_t)b * TT_ACC_STRIDE;
-      const int z = ((int)blockIdx.x + tl * (int)gridDim.x) / mt;
+      const TtTile t = tile_of(jobs, p.njob, (int)blockIdx.x + tl * (int)gridDim.x, mt);
       bool v0, v1;
-      const int nst = tile_stages(p, z, v0, v1);
+      const int nst = tile_stages(jobs[t.j], t.z, v0, v1);
       for (int st = 0; st < nst; ++st, ++it) {
         const int cs = it % TT_CS;
         if (!warp_wait(&conv_full[cs], (uint32_t)((it / TT_CS) & 1), abort_flag, p.wait_limit)) {
@@ -557,16 +594,18 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
     const int part = lane & 1;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
     const int nch = NB / 16;
-    const bool has_c0 = p.C0 != nullptr && p.beta != 0.f;
     for (int tl = 0; tl < ntl; ++tl) {
       const int b = tl & 1;
-      const int tile = (int)blockIdx.x + tl * (int)gridDim.x;
-      const int z = tile / mt;
-      const int row = (tile - z * mt) * TT_ROWS + l;
+      const TtTile t = tile_of(jobs, p.njob, (int)blockIdx.x + tl * (int)gridDim.x, mt);
+      const TtJob& qj = jobs[t.j];
+      const bool has_c0 = qj.C0 != nullptr && qj.beta != 0.f;
+      const float alpha = qj.alpha, beta = qj.beta;
+      const int z = t.z;
+      const int row = t.i0 + l;
       const bool rok = row < p.M;
-      float2* Crow = p.C + (int64_t)z * p.sC + (int64_t)(rok ? row : 0) * p.ldc;
+      float2* Crow = qj.C + (int64_t)z * qj.sC + (int64_t)(rok ? row : 0) * qj.ldc;
       const float2* C0row =
-          has_c0 ? p.C0 + (int64_t)z * p.sC0 + (int64_t)(rok ? row : 0) * p.ldc0 : nullptr;
+          has_c0 ? qj.C0 + (int64_t)z * qj.sC0 + (int64_t)(rok ? row : 0) * qj.ldc0 : nullptr;
       // C0 of chunk c: four 16-byte pieces, columns 16 c + 4 j + 2 part (+1)
       auto load_c0 = [&](int c, float4 (&dst)[4]) {
 #pragma unroll
@@ -582,7 +621,7 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
       if (!warp_wait(&acc_full[b], (uint32_t)((tl / 2) & 1), abort_flag, p.wait_limit)) break;
       fence_after();
       bool v0, v1;
-      const bool empty = tile_stages(p, z, v0, v1) == 0;  // no MMA: the product is zero
+      const bool empty = tile_stages(qj, z, v0, v1) == 0;  // no MMA: the product is zero
       for (int c = 0; c < nch; ++c) {
         float v[16];
         tmem_ld16(lane_base + (uint32_t)b * TT_ACC_STRIDE + 16u * (uint32_t)c, v);
@@ -609,15 +648,15 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
                           : make_float4(v[4 * j], r0, v[4 * j + 1], r1);
           const int col = 16 * c + 4 * j + 2 * part;
           if (rok && col < p.N) {
-            o.x *= p.alpha;
-            o.y *= p.alpha;
-            o.z *= p.alpha;
-            o.w *= p.alpha;
+            o.x *= alpha;
+            o.y *= alpha;
+            o.z *= alpha;
+            o.w *= alpha;
             if (has_c0) {
-              o.x = fmaf(p.beta, c0a[j].x, o.x);
-              o.y = fmaf(p.beta, c0a[j].y, o.y);
-              o.z = fmaf(p.beta, c0a[j].z, o.z);
-              o.w = fmaf(p.beta, c0a[j].w, o.w);
+              o.x = fmaf(beta, c0a[j].x, o.x);
+              o.y = fmaf(beta, c0a[j].y, o.y);
+              o.z = fmaf(beta, c0a[j].z, o.z);
+              o.w = fmaf(beta, c0a[j].w, o.w);
             }
             *reinterpret_cast<float4*>(Crow + col) = o;
           }
@@ -717,65 +756,83 @@ bool seg_maps(const TcSegment& g, int M, int N, int NB, CUtensorMap* mA, CUtenso
 
 }  // namespace
 
+cudaError_t launch_tc_cgemm_tma_jobs(int M, int N, int njob, const TcJob* jobs, int32_t* status,
+                                     long long wait_limit, cudaStream_t s) {
+  // the shapes and alignments the TMA boxes and the 16-byte epilogue stores need
+  if (M < 1 || N < 2 || N > TT_NMAX || (N & 1) || njob < 1 || njob > 2)
+    return cudaErrorNotSupported;
+  const int NB = (N + 15) & ~15;
+  const int mt = (M + TT_ROWS - 1) / TT_ROWS;
+  TtMaps maps{};
+  TtArgs a{};
+  a.M = M;
+  a.N = N;
+  a.NB = NB;
+  a.status = status;
+  a.wait_limit = wait_limit;
+  int64_t ntiles = 0;
+  for (int jb = 0; jb < njob; ++jb) {
+    const TcJob& jo = jobs[jb];
+    if (jo.batch <= 0) continue;  // an empty job takes no tiles
+    if (jo.batch > 65535 || jo.nseg < 1 || jo.nseg > 2) return cudaErrorNotSupported;
+    if (!al16(jo.C) || (jo.ldc & 1) || (jo.C0 && (!al16(jo.C0) || (jo.ldc0 & 1))))
+      return cudaErrorNotSupported;
+    TtJob& q = a.job[a.njob];
+    for (int g = 0; g < jo.nseg; ++g) {
+      const TcSegment& sg = jo.seg[g];
+      CUtensorMap* mA = &maps.m[4 * a.njob + 2 * g];
+      if (!seg_maps(sg, M, N, NB, mA, mA + 1)) return cudaErrorNotSupported;
+      // the members each output reads must exist
+      const int lo = sg.zlo < 0 ? 0 : sg.zlo, hi = sg.zhi > jo.batch ? jo.batch : sg.zhi;
+      if (hi > lo && (lo + sg.zA < 0 || hi - 1 + sg.zA >= sg.nA || lo + sg.zB < 0 ||
+                      hi - 1 + sg.zB >= sg.nB))
+        return cudaErrorNotSupported;
+      q.seg[g] = TtSeg{(sg.K + TT_KC - 1) / TT_KC, sg.zA, sg.zB, lo, hi, sg.ta ? 1 : 0,
+                       sg.tb ? 1 : 0};
+    }
+    q.batch = jo.batch;
+    q.nseg = jo.nseg;
+    q.tile0 = (int)ntiles;
+    q.C = jo.C;
+    q.ldc = jo.ldc;
+    q.sC = jo.sC;
+    q.C0 = jo.C0;
+    q.ldc0 = jo.ldc0;
+    q.sC0 = jo.sC0;
+    q.alpha = jo.alpha;
+    q.beta = jo.beta;
+    ntiles += (int64_t)jo.batch * mt;
+    ++a.njob;
+  }
+  if (a.njob == 0) return cudaSuccess;
+  a.ntiles = (int)ntiles;
+  const unsigned grid = (unsigned)(ntiles < sms() ? ntiles : sms());
+  RCI_CUDA_TRY(cudaFuncSetAttribute(tc_cgemm_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)TT_SMEM));
+  tc_cgemm_tma_kernel<<<grid, TT_THREADS, TT_SMEM, s>>>(maps, a);
+  rci_note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tc_cgemm_tma_seg(int M, int N, int nseg, const TcSegment* seg, float alpha,
                                     float beta, const float2* C0, int64_t ldc0, int64_t sC0,
                                     float2* C, int64_t ldc, int64_t sC, int batch, int32_t* status,
                                     long long wait_limit, cudaStream_t s) {
   if (batch <= 0) return cudaSuccess;
-  // the shapes and alignments the TMA boxes and the 16-byte epilogue stores need
-  if (M < 1 || N < 2 || N > TT_NMAX || (N & 1) || batch > 65535 || nseg < 1 || nseg > 2)
-    return cudaErrorNotSupported;
-  if (!al16(C) || (ldc & 1) || (C0 && (!al16(C0) || (ldc0 & 1)))) return cudaErrorNotSupported;
-  const int NB = (N + 15) & ~15;
-  CUtensorMap m[4];
-  TtArgs a{};
-  a.M = M;
-  a.N = N;
-  a.NB = NB;
-  a.batch = batch;
-  a.nseg = nseg;
-  for (int g = 0; g < nseg; ++g) {
-    const TcSegment& sg = seg[g];
-    if (!seg_maps(sg, M, N, NB, &m[2 * g], &m[2 * g + 1])) return cudaErrorNotSupported;
-    // the members each output reads must exist
-    const int lo = sg.zlo < 0 ? 0 : sg.zlo, hi = sg.zhi > batch ? batch : sg.zhi;
-    if (hi > lo && (lo + sg.zA < 0 || hi - 1 + sg.zA >= sg.nA || lo + sg.zB < 0 ||
-                    hi - 1 + sg.zB >= sg.nB))
-      return cudaErrorNotSupported;
-    a.seg[g] = TtSeg{(sg.K + TT_KC - 1) / TT_KC, sg.zA, sg.zB, lo, hi};
-  }
-  if (nseg == 1) {
-    m[2] = m[0];
-    m[3] = m[1];
-  }
-  a.C = C;
-  a.ldc = ldc;
-  a.sC = sC;
-  a.C0 = C0;
-  a.ldc0 = ldc0;
-  a.sC0 = sC0;
-  a.alpha = alpha;
-  a.beta = beta;
-  a.status = status;
-  a.wait_limit = wait_limit;
-  const int64_t ntiles = (int64_t)batch * ((M + TT_ROWS - 1) / TT_ROWS);
-  const unsigned grid = (unsigned)(ntiles < sms() ? ntiles : sms());
-  auto launch = [&](auto kern) -> cudaError_t {
-    RCI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TT_SMEM));
-    kern<<<grid, TT_THREADS, TT_SMEM, s>>>(m[0], m[1], m[2], m[3], a);
-    rci_note_launch();
-    return cudaGetLastError();
-  };
-  const bool ta0 = seg[0].ta, tb0 = seg[0].tb;
-  if (nseg == 2) {
-    // the one two-segment form the factorisation uses: (N, N) then (T, N)
-    if (ta0 || tb0 || !seg[1].ta || seg[1].tb) return cudaErrorNotSupported;
-    return launch(tc_cgemm_tma_kernel<false, false, true, false>);
-  }
-  if (!ta0 && !tb0) return launch(tc_cgemm_tma_kernel<false, false, false, false>);
-  if (!ta0 && tb0) return launch(tc_cgemm_tma_kernel<false, true, false, false>);
-  if (ta0 && !tb0) return launch(tc_cgemm_tma_kernel<true, false, false, false>);
-  return launch(tc_cgemm_tma_kernel<true, true, false, false>);
+  if (nseg < 1 || nseg > 2) return cudaErrorNotSupported;
+  TcJob jo{};
+  jo.nseg = nseg;
+  for (int g = 0; g < nseg; ++g) jo.seg[g] = seg[g];
+  jo.alpha = alpha;
+  jo.beta = beta;
+  jo.C0 = C0;
+  jo.ldc0 = ldc0;
+  jo.sC0 = sC0;
+  jo.C = C;
+  jo.ldc = ldc;
+  jo.sC = sC;
+  jo.batch = batch;
+  return launch_tc_cgemm_tma_jobs(M, N, 1, &jo, status, wait_limit, s);
 }
 
 cudaError_t launch_tc_cgemm_tma(int M, int N, int K, bool ta, bool tb, float alpha,

@@ -122,6 +122,14 @@ def test_multi_rhs_solve_matches_single(prec):
         assert np.max(np.abs(got[..., q] - ref[..., q])) <= TOL_F[prec] * np.max(np.abs(ref[..., q]))
 
 
+def _fp32_resolved(info, prec):
+    # an FP32 factorisation that is wrong still gives the right F through the FP64 fallback;
+    # these designs must be resolved by the FP32 one with a few plain refinement steps
+    if prec == P.FP32_REFINE:
+        assert not info.fallback, info
+        assert info.krylov_steps == 0 and info.refine_iters <= 6, info
+
+
 @pytest.mark.parametrize("prec", [P.FP64, P.FP32_REFINE])
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_avg_intensity_matches_oracle(name, prec):
@@ -132,6 +140,7 @@ def test_avg_intensity_matches_oracle(name, prec):
     F_ref, v_ref = ev.reciprocal()
     F, info = g.avg_intensity(wl.objective, wl.light)
     assert abs(F - F_ref) <= TOL_F[prec] * abs(F_ref), (F, F_ref, info)
+    _fp32_resolved(info, prec)
     v, _ = g.solve_reciprocal(wl.objective)
     v = _cplx(v)
     assert np.max(np.abs(v - v_ref)) <= TOL_F[prec] * np.max(np.abs(v_ref))
@@ -145,6 +154,7 @@ def test_avg_intensity_c1(prec):
     F_ref, v_ref = Evaluation(wl, ws).reciprocal()
     F, info = g.avg_intensity(wl.objective, wl.light)
     assert abs(F - F_ref) <= TOL_F[prec] * F_ref, (F, F_ref, info)
+    _fp32_resolved(info, prec)
 
 
 @pytest.mark.parametrize("prec", [P.FP32_REFINE, P.FP64])
@@ -156,6 +166,7 @@ def test_avg_intensity_c2_full_size(prec):
     F_ref, v_ref = Evaluation(wl, ws).reciprocal()
     F, info = g.avg_intensity(wl.objective, wl.light)
     assert abs(F - F_ref) <= TOL_F[prec] * F_ref, (F, F_ref, info)
+    _fp32_resolved(info, prec)
     v, _ = g.solve_reciprocal(wl.objective)
     v = _cplx(v)                              # the whole source-plane field, 4000 points
     assert v.shape == v_ref.shape
