@@ -138,12 +138,15 @@ __device__ __forceinline__ void tri_backward(const TriRow<T>& f, int n, Load loa
   }
 }
 
-// Forward sweep for the unit vector e_b into column ycol (stride ny).
+// Forward sweep for the unit vector e_b into column ycol (stride ny).  Rows j < b - 1 of the
+// sweep are exactly zero (the carried value stays zero until the unit entry is reached), so
+// the sweep starts at row max(b - 1, 0) and writes only rows from there on; readers take the
+// rows above as zero.
 template <typename T>
 __device__ __forceinline__ void tri_forward_unit(const TriRow<T>& f, int n, int b,
-                                                 cplx<T>* __restrict__ ycol, int ny) {
+                                                 cplx<T>* ycol, int ny) {
   cplx<T> cur = b == 0 ? mkc(T(1), T(0)) : czero<T>();
-  for (int j = 0; j < n - 1; ++j) {
+  for (int j = b > 0 ? b - 1 : 0; j < n - 1; ++j) {
     const cplx<T> nb = (j + 1 == b) ? mkc(T(1), T(0)) : czero<T>();
     if (f.piv[j]) {
       ycol[(int64_t)j * ny] = nb;
@@ -159,24 +162,23 @@ __device__ __forceinline__ void tri_forward_unit(const TriRow<T>& f, int n, int 
 // Dense Schur blocks of the first reduced system, one block per kept row e = 2k:
 //   D'_k = T_e - diag(cx[e-1]) T_{e-1}^{-1} diag(cx[e-1]) - diag(cx[e]) T_{e+1}^{-1} diag(cx[e])
 //   L'_k = -diag(cx[e-1]) T_{e-1}^{-1} diag(cx[e-2])
-// Thread b forms column b of T^{-1} by a tridiagonal solve with the unit vector e_b; the
-// forward sweep goes to a separate scratch column so the backward sweep's loads do not
-// wait on its own stores.
-// Dense Schur blocks of the first reduced system, one block per kept row e = 2k:
-//   D'_k = T_e - diag(cx[e-1]) T_{e-1}^{-1} diag(cx[e-1]) - diag(cx[e]) T_{e+1}^{-1} diag(cx[e])
-//   L'_k = -diag(cx[e-1]) T_{e-1}^{-1} diag(cx[e-2])
 // Thread b forms column b of both inverses: the forward sweeps of the unit vector e_b go to
-// two scratch columns (YR, YL: the next level's free working arrays), then one backward
-// sweep runs both recurrences side by side, so that every entry of D'_k is formed in one
-// step (no read-back of a partial D'), with the scratch loads issued a few rows ahead.
-template <typename T>
+// two scratch columns (YR, YL: the next level's free working arrays; only the rows from
+// b - 1 on, the others being zero), then one backward sweep runs both recurrences side by
+// side, so that every entry of D'_k is formed in one step (no read-back of a partial D'),
+// with the scratch loads issued a few rows ahead.
+// MODE 1 forms instead the dense T_{2k+1}^{-1} of the eliminated rows k < m0 (the stored
+// inverses of the solve with several right-hand sides), one block each, the forward sweep
+// written in place into the output column: the backward sweep reads row a - PF before it
+// writes row a, so every row is read before it is overwritten.
+template <typename T, int MODE>
 __global__ void level0_schur_kernel(const double2* __restrict__ dg, const double2* __restrict__ cx,
-                                    const double2* __restrict__ cy, int nx, int ny, int m0,
+                                    const double2* __restrict__ cy, int nx, int ny,
                                     const cplx<T>* __restrict__ tdl, const cplx<T>* __restrict__ tdinv,
                                     const cplx<T>* __restrict__ tdu, const cplx<T>* __restrict__ tdu2,
                                     const uint8_t* __restrict__ tpiv, cplx<T>* __restrict__ Dn,
-                                    cplx<T>* __restrict__ Ln, cplx<T>* __restrict__ scrR,
-                                    cplx<T>* __restrict__ scrL, cplx<T>* __restrict__ G0) {
+                                    cplx<T>* __restrict__ Ln, cplx<T>* scrR,
+                                    cplx<T>* __restrict__ scrL, cplx<T>* G0) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   cplx<T>* sm = reinterpret_cast<cplx<T>*>(sm_raw);
   // [0,4ny): right factors, [4ny,8ny): left factors, then cxl2, cxl, cxr, dge, cye; piv bytes last
@@ -192,8 +194,8 @@ __global__ void level0_schur_kernel(const double2* __restrict__ dg, const double
 
   const int k = blockIdx.x;
   const int64_t e = 2 * (int64_t)k;
-  const bool has_r = e + 1 < nx;   // eliminated row e+1 has index k
-  const bool has_l = e >= 1;       // eliminated row e-1 has index k-1
+  const bool has_r = MODE == 1 || e + 1 < nx;   // eliminated row e+1 has index k
+  const bool has_l = MODE == 0 && e >= 1;       // eliminated row e-1 has index k-1
   for (int j = threadIdx.x; j < ny; j += blockDim.x) {
     if (has_r) {
       int64_t b = (int64_t)k * ny + j;
@@ -202,10 +204,9 @@ __global__ void level0_schur_kernel(const double2* __restrict__ dg, const double
       R[2 * ny + j] = tdu[b];
       R[3 * ny + j] = tdu2[b];
       pivR[j] = tpiv[b];
-      cxr[j] = ccast<T>(cx[e * ny + j]);
-    } else {
-      cxr[j] = czero<T>();
     }
+    if (MODE == 1) continue;
+    cxr[j] = has_r ? ccast<T>(cx[e * ny + j]) : czero<T>();
     if (has_l) {
       int64_t b = (int64_t)(k - 1) * ny + j;
       Lf[j] = tdl[b];
@@ -227,14 +228,18 @@ __global__ void level0_schur_kernel(const double2* __restrict__ dg, const double
   const int64_t nn = (int64_t)ny * ny;
   cplx<T>* __restrict__ Dcol = Dn + (int64_t)k * nn + b;
   cplx<T>* __restrict__ Lcol = Ln + (int64_t)k * nn + b;
-  cplx<T>* __restrict__ YR = scrR + (int64_t)k * nn + b;
+  cplx<T>* Gcol = G0 + (int64_t)k * nn + b;
+  // MODE 1: the sweep in place in the output column
+  cplx<T>* YR = MODE == 1 ? Gcol : scrR + (int64_t)k * nn + b;
   cplx<T>* __restrict__ YL = scrL + (int64_t)k * nn + b;
-  cplx<T>* __restrict__ Gcol = G0 + (int64_t)k * nn + b;
   const TriRow<T> fR{R, R + ny, R + 2 * ny, R + 3 * ny, pivR};
   const TriRow<T> fL{Lf, Lf + ny, Lf + 2 * ny, Lf + 3 * ny, pivL};
   if (has_r) tri_forward_unit<T>(fR, ny, b, YR, ny);
   if (has_l) tri_forward_unit<T>(fL, ny, b, YL, ny);
-  const cplx<T> sb = cxr[b], sl = cxl[b], sl2 = cxl2[b];
+  const int a_lo = b > 0 ? b - 1 : 0;  // first row the sweeps wrote
+  const cplx<T> sb = MODE == 0 ? cxr[b] : czero<T>();
+  const cplx<T> sl = MODE == 0 ? cxl[b] : czero<T>();
+  const cplx<T> sl2 = MODE == 0 ? cxl2[b] : czero<T>();
   cplx<T> r1 = czero<T>(), r2 = czero<T>(), l1 = czero<T>(), l2 = czero<T>();
   // scratch values of the next PF rows, loaded ahead of the recurrences
   constexpr int PF = 4;
@@ -242,8 +247,8 @@ __global__ void level0_schur_kernel(const double2* __restrict__ dg, const double
 #pragma unroll
   for (int q = 0; q < PF; ++q) {
     const int a = ny - 1 - q;
-    yr[q] = (has_r && a >= 0) ? YR[(int64_t)a * ny] : czero<T>();
-    yl[q] = (has_l && a >= 0) ? YL[(int64_t)a * ny] : czero<T>();
+    yr[q] = (has_r && a >= a_lo) ? YR[(int64_t)a * ny] : czero<T>();
+    yl[q] = (has_l && a >= a_lo) ? YL[(int64_t)a * ny] : czero<T>();
   }
   for (int a0 = ny - 1; a0 >= 0; a0 -= PF) {
 #pragma unroll
@@ -252,24 +257,33 @@ __global__ void level0_schur_kernel(const double2* __restrict__ dg, const double
       if (a < 0) break;
       const cplx<T> cr = yr[q], cl = yl[q];
       const int an = a - PF;  // the row PF steps ahead into the same ring slot
-      yr[q] = (has_r && an >= 0) ? YR[(int64_t)an * ny] : czero<T>();
-      yl[q] = (has_l && an >= 0) ? YL[(int64_t)an * ny] : czero<T>();
+      yr[q] = (has_r && an >= a_lo) ? YR[(int64_t)an * ny] : czero<T>();
+      yl[q] = (has_l && an >= a_lo) ? YL[(int64_t)an * ny] : czero<T>();
       // T_{e+1}^{-1} and T_{e-1}^{-1}, entry (a, b)
       cplx<T> gr = cfms(fR.du2[a], r2, cfms(fR.du[a], r1, cr)) * fR.dinv[a];
-      cplx<T> gl = cfms(fL.du2[a], l2, cfms(fL.du[a], l1, cl)) * fL.dinv[a];
       if (!has_r) gr = czero<T>();
-      if (!has_l) gl = czero<T>();
       r2 = r1;
       r1 = gr;
+      if (MODE == 1) {
+        Gcol[(int64_t)a * ny] = gr;
+        continue;
+      }
+      cplx<T> gl = cfms(fL.du2[a], l2, cfms(fL.du[a], l1, cl)) * fL.dinv[a];
+      if (!has_l) gl = czero<T>();
       l2 = l1;
       l1 = gl;
       const cplx<T> te = a == b ? dge[a] : (a == b - 1 ? cye[a] : (a == b + 1 ? cye[b] : czero<T>()));
       const cplx<T> cgl = cxl[a] * gl;
       Dcol[(int64_t)a * ny] = cfms(cgl, sl, cfms(cxr[a] * gr, sb, te));
-      if (has_r) Gcol[(int64_t)a * ny] = gr;  // T_{e+1}^{-1}, kept for the solve
       if (has_l) Lcol[(int64_t)a * ny] = -(cgl * sl2);
     }
   }
+}
+
+// shared memory of level0_schur_kernel: 13 ny complex values and 2 ny pivot flags
+template <typename T>
+inline size_t l0_smem(int ny) {
+  return (size_t)13 * ny * sizeof(cplx<T>) + 2 * (size_t)ny;
 }
 
 // ===================================================================== Gauss-Jordan
@@ -1362,9 +1376,7 @@ __global__ void copy_kept_kernel(const cplx<T>* __restrict__ xup, cplx<T>* __res
   xl[2 * k * row + r] = xup[tt];
 }
 
-// ----- single right-hand side: matrix-vector kernels, one block per eliminated row
-constexpr int GV_THREADS = 256, GV_WARPS = GV_THREADS / 32;
-
+// sum of a complex value over the 32 lanes of a warp (every lane gets the sum)
 template <typename T>
 __device__ __forceinline__ cplx<T> warp_sum(cplx<T> v) {
   for (int off = 16; off > 0; off >>= 1) {
@@ -1372,70 +1384,6 @@ __device__ __forceinline__ cplx<T> warp_sum(cplx<T> v) {
     v.y += __shfl_xor_sync(0xffffffffu, v.y, off);
   }
   return v;
-}
-
-// y = M x (M row-major ny x ny, x in shared memory).  FP32 rows of even length are read
-// two complex values per 16-byte load.
-template <typename T>
-__device__ void gemv_n(const cplx<T>* __restrict__ M, const cplx<T>* x, cplx<T>* y, int ny) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int a = warp; a < ny; a += GV_WARPS) {
-    cplx<T> acc = czero<T>();
-    const cplx<T>* Mr = M + (int64_t)a * ny;
-    if constexpr (sizeof(T) == 4) {
-      if ((ny & 1) == 0) {
-        const float4* M4 = reinterpret_cast<const float4*>(Mr);
-        for (int c2 = lane; c2 < ny / 2; c2 += 32) {
-          const float4 v = __ldg(M4 + c2);
-          acc = cfma(mkc(v.x, v.y), x[2 * c2], acc);
-          acc = cfma(mkc(v.z, v.w), x[2 * c2 + 1], acc);
-        }
-      } else {
-        for (int c = lane; c < ny; c += 32) acc = cfma(Mr[c], x[c], acc);
-      }
-    } else {
-      for (int c = lane; c < ny; c += 32) acc = cfma(Mr[c], x[c], acc);
-    }
-    acc = warp_sum<T>(acc);
-    if (lane == 0) y[a] = acc;
-  }
-}
-
-// Level 0 forward, one right-hand side: t0[k] = T_{2k+1}^{-1} b[2k+1] (stored inverses).
-template <typename T>
-__global__ void __launch_bounds__(GV_THREADS)
-fwd0_gemv_kernel(const cplx<T>* __restrict__ G0, const cplx<T>* __restrict__ b,
-                 cplx<T>* __restrict__ t0, int ny) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  cplx<T>* bs = reinterpret_cast<cplx<T>*>(sm_raw);
-  const int64_t k = blockIdx.x;
-  for (int c = threadIdx.x; c < ny; c += GV_THREADS) bs[c] = b[(2 * k + 1) * ny + c];
-  __syncthreads();
-  gemv_n<T>(G0 + k * ny * ny, bs, t0 + k * ny, ny);
-}
-
-// Level 0 backward, one right-hand side: x[2k] = x1[k];
-// x[2k+1] = T^{-1} (b[2k+1] - cx[2k] o x1[k] - cx[2k+1] o x1[k+1]).  b may alias x: row
-// 2k+1 of b is read into shared memory before row 2k+1 of x is written.
-template <typename T>
-__global__ void __launch_bounds__(GV_THREADS)
-bwd0_gemv_kernel(const cplx<T>* __restrict__ G0, const cplx<T>* b, const cplx<T>* __restrict__ x1,
-                 const double2* __restrict__ cx, cplx<T>* x, int nx, int ny) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  cplx<T>* rhs = reinterpret_cast<cplx<T>*>(sm_raw);
-  const int64_t k = blockIdx.x, r = 2 * k + 1;
-  const bool has = r < nx, has_b = r + 1 < nx;
-  for (int c = threadIdx.x; c < ny; c += GV_THREADS) {
-    const cplx<T> xa = x1[k * ny + c];
-    if (has) {
-      cplx<T> v = cfms(ccast<T>(cx[(r - 1) * ny + c]), xa, b[r * ny + c]);
-      if (has_b) v = cfms(ccast<T>(cx[r * ny + c]), x1[(k + 1) * ny + c], v);
-      rhs[c] = v;
-    }
-    x[2 * k * ny + c] = xa;
-  }
-  __syncthreads();
-  if (has) gemv_n<T>(G0 + k * ny * ny, rhs, x + r * ny, ny);
 }
 
 // Level 0 backward, several right-hand sides: x[2k] = x1[k] and the right-hand sides of
@@ -1458,100 +1406,6 @@ __global__ void bwd0_rhs_kernel(const cplx<T>* b, const cplx<T>* __restrict__ x1
   }
   x[2 * k * row + e] = xa;
 }
-
-// y = M^T x, columns spread over lanes, rows over warps, reduced through shared memory
-template <typename T, int CMAX>
-__device__ void gemv_t(const cplx<T>* __restrict__ M, const cplx<T>* x, cplx<T>* red, cplx<T>* y,
-                       int ny) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  cplx<T> acc[CMAX];
-#pragma unroll
-  for (int s = 0; s < CMAX; ++s) acc[s] = czero<T>();
-  for (int a = warp; a < ny; a += GV_WARPS) {
-    const cplx<T> xa = x[a];
-    const cplx<T>* Mr = M + (int64_t)a * ny;
-#pragma unroll
-    for (int s = 0; s < CMAX; ++s) {
-      int c = lane + 32 * s;
-      if (c < ny) acc[s] = cfma(Mr[c], xa, acc[s]);
-    }
-  }
-#pragma unroll
-  for (int s = 0; s < CMAX; ++s) {
-    int c = lane + 32 * s;
-    if (c < ny) red[warp * ny + c] = acc[s];
-  }
-  __syncthreads();
-  for (int c = threadIdx.x; c < ny; c += GV_THREADS) {
-    cplx<T> v = czero<T>();
-    for (int w = 0; w < GV_WARPS; ++w) v = v + red[w * ny + c];
-    y[c] = v;
-  }
-  __syncthreads();
-}
-
-template <typename T, int CMAX>
-__global__ void __launch_bounds__(GV_THREADS)
-fwd_gemv_kernel(const cplx<T>* __restrict__ Dinv, const cplx<T>* __restrict__ X,
-                const cplx<T>* __restrict__ Y, const cplx<T>* __restrict__ B,
-                cplx<T>* __restrict__ t, cplx<T>* __restrict__ P, cplx<T>* __restrict__ Q, int n,
-                int ny) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  cplx<T>* bs = reinterpret_cast<cplx<T>*>(sm_raw);
-  cplx<T>* red = bs + ny;
-  const int64_t k = blockIdx.x;
-  const int64_t nn = (int64_t)ny * ny;
-  for (int c = threadIdx.x; c < ny; c += GV_THREADS) bs[c] = B[(2 * k + 1) * ny + c];
-  __syncthreads();
-  gemv_n<T>(Dinv + k * nn, bs, t + k * ny, ny);
-  gemv_t<T, CMAX>(X + k * nn, bs, red, P + k * ny, ny);
-  if (2 * k + 2 < n) gemv_t<T, CMAX>(Y + k * nn, bs, red, Q + k * ny, ny);
-}
-
-// x_l[2k] = x_up[k];  x_l[2k+1] = t[k] - X_k x_up[k] - Y_k x_up[k+1]
-template <typename T>
-__global__ void __launch_bounds__(GV_THREADS)
-bwd_gemv_kernel(const cplx<T>* __restrict__ X, const cplx<T>* __restrict__ Y,
-                const cplx<T>* __restrict__ t, const cplx<T>* __restrict__ xup,
-                cplx<T>* __restrict__ xl, int n, int m, int ny) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  cplx<T>* xa = reinterpret_cast<cplx<T>*>(sm_raw);
-  cplx<T>* xb = xa + ny;
-  const int64_t k = blockIdx.x;
-  const int64_t nn = (int64_t)ny * ny;
-  const bool has_b = 2 * k + 2 < n;
-  for (int c = threadIdx.x; c < ny; c += GV_THREADS) {
-    cplx<T> v = xup[k * ny + c];
-    xa[c] = v;
-    xl[2 * k * ny + c] = v;
-    xb[c] = has_b ? xup[(k + 1) * ny + c] : czero<T>();
-  }
-  __syncthreads();
-  if (k >= m) return;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const cplx<T>* Xk = X + k * nn;
-  const cplx<T>* Yk = Y + k * nn;
-  for (int a = warp; a < ny; a += GV_WARPS) {
-    cplx<T> acc = czero<T>();
-    for (int c = lane; c < ny; c += 32) {
-      acc = cfma(Xk[(int64_t)a * ny + c], xa[c], acc);
-      if (has_b) acc = cfma(Yk[(int64_t)a * ny + c], xb[c], acc);
-    }
-    acc = warp_sum<T>(acc);
-    if (lane == 0) xl[(2 * k + 1) * ny + a] = t[k * ny + a] - acc;
-  }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(GV_THREADS)
-final_gemv_kernel(const cplx<T>* __restrict__ Dinv, const cplx<T>* B, cplx<T>* x, int ny) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  cplx<T>* bs = reinterpret_cast<cplx<T>*>(sm_raw);
-  for (int c = threadIdx.x; c < ny; c += GV_THREADS) bs[c] = B[c];
-  __syncthreads();
-  gemv_n<T>(Dinv, bs, x, ny);
-}
-
 
 // ----- single right-hand side, chunked: a block per (block row k, chunk of RC rows or
 // columns), so that even the last reduction levels spread over many SMs, and every lane
@@ -1890,32 +1744,6 @@ mv_chunk_kernel(const cplx<T>* __restrict__ M, const cplx<T>* __restrict__ V, in
   rows_mv<T, SMAX>(M + k * (int64_t)ny * ny, vs, ny, blockIdx.y * RC, y + k * ny, nullptr);
 }
 
-// Level 0 backward with stored inverses: x[2k] = x1[k];
-// x[2k+1] = G_k (b[2k+1] - cx[2k] o x1[k] - cx[2k+1] o x1[k+1]) on the chunk rows.
-// b must not alias x (other blocks of the same k still read row 2k+1 of b).
-template <typename T, int SMAX>
-__global__ void __launch_bounds__(CH_THREADS)
-bwd0_chunk_kernel(const cplx<T>* __restrict__ G0, const cplx<T>* __restrict__ b,
-                  const cplx<T>* __restrict__ x1, const double2* __restrict__ cx,
-                  cplx<T>* __restrict__ x, int nx, int ny) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  cplx<T>* rhs = reinterpret_cast<cplx<T>*>(sm_raw);
-  const int64_t k = blockIdx.x, r = 2 * k + 1;
-  const int c0 = blockIdx.y * RC;
-  const bool has = r < nx, has_b = r + 1 < nx;
-  for (int c = threadIdx.x; c < ny; c += CH_THREADS) {
-    if (has) {
-      cplx<T> v = cfms(ccast<T>(cx[(r - 1) * ny + c]), x1[k * ny + c], b[r * ny + c]);
-      if (has_b) v = cfms(ccast<T>(cx[r * ny + c]), x1[(k + 1) * ny + c], v);
-      rhs[c] = v;
-    }
-  }
-  for (int c = c0 + threadIdx.x; c < c0 + RC && c < ny; c += CH_THREADS)
-    x[2 * k * ny + c] = x1[k * ny + c];
-  __syncthreads();
-  if (has) rows_mv<T, SMAX>(G0 + k * (int64_t)ny * ny, rhs, ny, c0, x + r * ny, nullptr);
-}
-
 // ----- single right-hand side, level 0 by the pivoted tridiagonal factors (5 ny values per
 // eliminated row instead of the dense ny x ny inverse): one warp per eliminated row k stages
 // the row's factors and right-hand side in shared memory, lane 0 runs the forward and
@@ -1992,6 +1820,7 @@ struct BcrHandle {
   void *tdl = nullptr, *tdinv = nullptr, *tdu = nullptr, *tdu2 = nullptr;
   uint8_t* tpiv = nullptr;
   void* G0 = nullptr;             // dense T_r^{-1} of the level-0 eliminated rows (m0 x ny x ny)
+  bool g0_valid = false;          // G0 holds the inverses of the current factorisation
   void* Dw[2] = {nullptr, nullptr};
   void* Lw[2] = {nullptr, nullptr};
   void* store = nullptr;
@@ -2132,18 +1961,21 @@ static cudaError_t factor_t(BcrHandle* h, const double2* dg, const double2* cx, 
     RCI_CUDA_TRY(cudaGetLastError());
   }
   {
-    int thr = (int)ceil_div(ny, 32) * 32;
-    size_t smem = (size_t)13 * ny * sizeof(cplx<T>) + 2 * (size_t)ny;
+    // D' and L' of the first reduced system; the stored inverses G0 are formed when a solve
+    // with several right-hand sides first needs them
+    const int thr = (int)ceil_div(ny, 32) * 32;
+    const size_t smem = l0_smem<T>(ny);
     if (smem > 48 * 1024)
-      RCI_CUDA_TRY(cudaFuncSetAttribute(level0_schur_kernel<T>,
+      RCI_CUDA_TRY(cudaFuncSetAttribute(level0_schur_kernel<T, 0>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // the next level's working arrays are free during level 0 and serve as scratch
-    level0_schur_kernel<T><<<n1, thr, smem, s>>>(dg, cx, cy, nx, ny, m0, tdl, tdinv, tdu, tdu2,
-                                                 h->tpiv, (cplx<T>*)h->Dw[0], (cplx<T>*)h->Lw[0],
-                                                 (cplx<T>*)h->Dw[1], (cplx<T>*)h->Lw[1],
-                                                 (cplx<T>*)h->G0);
+    level0_schur_kernel<T, 0><<<n1, thr, smem, s>>>(dg, cx, cy, nx, ny, tdl, tdinv, tdu, tdu2,
+                                                    h->tpiv, (cplx<T>*)h->Dw[0], (cplx<T>*)h->Lw[0],
+                                                    (cplx<T>*)h->Dw[1], (cplx<T>*)h->Lw[1],
+                                                    (cplx<T>*)h->G0);
     rci_note_launch();
     RCI_CUDA_TRY(cudaGetLastError());
+    h->g0_valid = false;
   }
   delete l0;
   const cplx<T> one = mkc(T(1), T(0)), mone = mkc(T(-1), T(0)), zero = czero<T>();
@@ -2409,6 +2241,22 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
   }
 
   // ================= several right-hand sides: batched GEMMs per level
+  // ---- the stored inverses of level 0, formed once per factorisation
+  if (m0 > 0 && !h->g0_valid) {
+    const int thr = (int)ceil_div(ny, 32) * 32;
+    const size_t smem = l0_smem<T>(ny);
+    if (smem > 48 * 1024)
+      RCI_CUDA_TRY(cudaFuncSetAttribute(level0_schur_kernel<T, 1>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cplx<T>* g0w = (cplx<T>*)h->G0;
+    level0_schur_kernel<T, 1><<<m0, thr, smem, s>>>(nullptr, nullptr, nullptr, nx, ny,
+                                                    (const cplx<T>*)h->tdl, (const cplx<T>*)h->tdinv,
+                                                    (const cplx<T>*)h->tdu, (const cplx<T>*)h->tdu2,
+                                                    h->tpiv, g0w, g0w, g0w, g0w, g0w);
+    rci_note_launch();
+    RCI_CUDA_TRY(cudaGetLastError());
+    h->g0_valid = true;
+  }
   // ---- level 0 forward: t0[k] = T_{2k+1}^{-1} b[2k+1] with the stored inverses
   if (m0 > 0)
     RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, one, G0, ny, nn, b + row, nrhs, 2 * row, zero,

@@ -103,6 +103,8 @@ def test_solve_matches_oracle(name, prec):
     x, info = g.solve(torch.from_numpy(b.ravel()).cuda())
     got = _cplx(x).reshape(og.nx, og.ny)
     assert np.max(np.abs(got - ref)) <= TOL_F[prec] * np.max(np.abs(ref)), info
+    # resolved by the FP32 factorisation itself, not by the FP64 fallback
+    assert not info.fallback and info.refine_iters <= 10, info
 
 
 @pytest.mark.parametrize("prec", [P.FP64, P.FP32_REFINE])
@@ -116,10 +118,39 @@ def test_multi_rhs_solve_matches_single(prec):
     nq = 5
     b = rng.standard_normal((og.nx, og.ny, nq)) + 1j * rng.standard_normal((og.nx, og.ny, nq))
     ref = s.solve(b)
-    x, _ = g.solve(torch.from_numpy(b.ravel()).cuda(), nrhs=nq)
+    x, info = g.solve(torch.from_numpy(b.ravel()).cuda(), nrhs=nq)
     got = _cplx(x).reshape(og.nx, og.ny, nq)
     for q in range(nq):
         assert np.max(np.abs(got[..., q] - ref[..., q])) <= TOL_F[prec] * np.max(np.abs(ref[..., q]))
+    # the stored level-0 inverses (formed on first use in FP32) resolve the system
+    # without the FP64 fallback
+    assert not info.fallback and info.refine_iters <= 10, info
+    # a second solve on the same factorisation reuses them and gives the same bits
+    x2, _ = g.solve(torch.from_numpy(b.ravel()).cuda(), nrhs=nq)
+    assert torch.equal(x, x2)
+
+
+def test_multi_rhs_solve_after_refactor_uses_the_new_inverses():
+    # the stored level-0 inverses belong to one factorisation: after a new design is
+    # factored, a solve with several right-hand sides must not reuse the previous ones
+    wl = CASES["ragged"]()
+    g, _ = _grid(wl, P.FP32_REFINE, seed=0)
+    g.factor()
+    og = OGrid(wl.grid)
+    rng = np.random.default_rng(5)
+    nq = 3
+    b = rng.standard_normal((og.nx, og.ny, nq)) + 1j * rng.standard_normal((og.nx, og.ny, nq))
+    bt = torch.from_numpy(b.ravel()).cuda()
+    g.solve(bt, nrhs=nq)
+    ws1 = _widths(wl, 1)
+    g.set_design(ws1)
+    g.factor()
+    x, info = g.solve(bt, nrhs=nq)
+    ref = Solver(og, rasterize_eps(og, ws1)).solve(b)
+    got = _cplx(x).reshape(og.nx, og.ny, nq)
+    for q in range(nq):
+        assert np.max(np.abs(got[..., q] - ref[..., q])) <= 1e-8 * np.max(np.abs(ref[..., q]))
+    assert not info.fallback and info.refine_iters <= 10, info
 
 
 def _fp32_resolved(info, prec):
