@@ -506,7 +506,8 @@ def run_ours(args):
                               % (g.device_bytes() / 1e9),
                            refine_iters_mean=round(sum(i.refine_iters for i in infos) / K, 2),
                            rel_residual_max=max(i.rel_residual for i in infos),
-                           fp64_fallbacks=sum(1 for i in infos if i.fallback)),
+                           fp64_fallbacks=sum(1 for i in infos if i.fallback),
+                           simt_refactors=sum(1 for i in infos if i.simt_refactor)),
             "measured_peaks": {k: (round(v, 3) if isinstance(v, float) else v)
                                for k, v in (live or {}).items()},
             "gpu_launches": int(launches),
@@ -718,6 +719,7 @@ def _serve_stream(P, W, local, n_requests, slots, arena_gb, cache_gb, repeat, ra
     span = (max(r["t_end_us"] for r in res) - min(r["t_submit_us"] for r in res)) * 1e-6
     grad = np.array([q.want_grad for q in reqs])
     fb = np.array([bool(r.get("fp64_fallback", 0)) for r in res])
+    sr = np.array([bool(r.get("simt_refactor", 0)) for r in res])
     delta = ("submitted", "completed", "failed", "admission_waits", "bypasses", "cache_hits",
              "cache_evictions")
     return {
@@ -728,6 +730,7 @@ def _serve_stream(P, W, local, n_requests, slots, arena_gb, cache_gb, repeat, ra
         "p99_queue_ms": round(float(np.percentile(wait, 99)), 3),
         "p50_ms_gradient": round(float(np.percentile(lat[grad], 50)), 3) if grad.any() else None,
         "fp64_fallbacks": int(fb.sum()),
+        "simt_refactors": int(sr.sum()),
         "p99_ms_fp32_only": round(float(np.percentile(lat[~fb], 99)), 3) if (~fb).any() else None,
         "requests": len(reqs), "failed": len(reqs) - sum(ok), "unconverged": unconverged,
         "status_counts": status_counts, "repeated_designs": round(repeat, 3),

@@ -141,7 +141,10 @@ typedef struct {
   int32_t krylov_steps;  /* FP32_REFINE: preconditioned steps of the Krylov refinement taken
                             after plain refinement stalled (0: plain refinement sufficed);
                             they are included in refine_iters */
-  int32_t reserved;
+  int32_t simt_refactor; /* FP32_REFINE: 1 when the design was factored again on the FP32 SIMT
+                            pipe because its tensor-core factorisation could not resolve it
+                            (see rci_set_refinement); refine_iters and krylov_steps are then
+                            those of the solve on that factorisation */
 } rci_info;
 
 typedef struct rci_grid rci_grid;
@@ -186,10 +189,14 @@ rci_status rci_solve(rci_grid* g, const double* b, double* x, int64_t nrhs, rci_
  * (restarted every 16 steps; each step one FP32 solve, counted in the same max_steps
  * budget; rci_info.krylov_steps).
  * An FP32_REFINE grid whose refinement fails -- a non-finite residual, plain and Krylov
- * refinement both stalled or out of steps, or a zero FP32 pivot in rci_factor -- factors
- * the current design once in FP64
+ * refinement both stalled or out of steps, or a zero FP32 pivot in rci_factor -- first
+ * factors the current design again in FP32 on the SIMT pipe (one rounding per FMA where
+ * the tensor-core factorisation rounds its 3xTF32 products about 3.5 times more coarsely)
+ * and repeats the solve on it (rci_info.simt_refactor); if that fails too, it factors the
+ * design once in FP64
  * (the FP64 factor store is allocated the first time, from the grid's memory source)
  * and finishes this and every later solve of that design on it (rci_info.fallback).
+ * The next rci_set_design returns the grid to the tensor-core factorisation.
  * A solve that ends above tol returns RCI_ENOCONV with its best value (FP64 and fallback
  * solves only above 1e-9).  tol > 0, 0 <= max_steps <= 100. */
 rci_status rci_set_refinement(rci_grid* g, double tol, int32_t max_steps);
@@ -371,6 +378,9 @@ typedef struct {
   double t_start_us;      /* admitted (grid ready) */
   double t_end_us;        /* result ready */
   uint64_t footprint;     /* device bytes of the request's grid */
+  int32_t simt_refactor;  /* 1: the design was factored again on the FP32 SIMT pipe
+                             (rci_info.simt_refactor) */
+  int32_t reserved;
 } rci_result;
 
 typedef struct {

@@ -1089,10 +1089,11 @@ __global__ void block_maxabs_kernel(const cplx<T>* __restrict__ a, int64_t strid
 
 template <typename T>
 cudaError_t launch_gj(cplx<T>* src, int64_t src_stride, cplx<T>* out, int64_t out_stride, int n,
-                      int batch, int32_t* status, cudaStream_t s, uint32_t* maxabs = nullptr) {
+                      int batch, int32_t* status, cudaStream_t s, uint32_t* maxabs = nullptr,
+                      bool tc = true) {
   if (batch <= 0) return cudaSuccess;
   if constexpr (sizeof(T) == 4) {
-    if (n <= 160)
+    if (tc && n <= 160)
       return launch_tc_gj(src, src_stride, out, out_stride, n, batch, status, s, maxabs);
   }
   if (maxabs) {
@@ -1821,6 +1822,7 @@ struct BcrHandle {
   uint8_t* tpiv = nullptr;
   void* G0 = nullptr;             // dense T_r^{-1} of the level-0 eliminated rows (m0 x ny x ny)
   bool g0_valid = false;          // G0 holds the inverses of the current factorisation
+  bool simt = false;              // FP32: factor and multi-RHS products on the SIMT pipe
   void* Dw[2] = {nullptr, nullptr};
   void* Lw[2] = {nullptr, nullptr};
   void* store = nullptr;
@@ -1853,6 +1855,12 @@ void bcr_destroy(BcrHandle* h) {
 size_t bcr_bytes(const BcrHandle* h) { return h->factor_bytes + h->ws_bytes; }
 void bcr_set_profiler(BcrHandle* h, Profiler* p) { h->prof = p; }
 int bcr_precision(const BcrHandle* h) { return h->prec; }
+void bcr_set_simt(BcrHandle* h, bool simt) { h->simt = simt && h->prec != RCI_FP64; }
+bool bcr_simt(const BcrHandle* h) { return h->simt; }
+
+// The status word handed to gemm<T>: its tensor-core paths run only with one (they record an
+// expired bounded wait there), so a handle set to the SIMT pipe passes none.
+static int32_t* gemm_status(const BcrHandle* h) { return h->simt ? nullptr : h->status; }
 
 cudaError_t bcr_create(int nx, int ny, int prec, const DevMem* mem, BcrHandle** out, size_t* bytes) {
   *out = nullptr;
@@ -1994,7 +2002,8 @@ static cudaError_t factor_t(BcrHandle* h, const double2* dg, const double2* cx, 
     // D_r^{-1} for the odd rows (the working copy of D_r is destroyed)
     {
       ProfScope ps(h->prof, PF_INVERT, s, 8.0 * ny * (double)nn * m, 2.0 * m * nn * sizeof(cplx<T>), 1);
-      RCI_CUDA_TRY(launch_gj<T>(D + nn, 2 * nn, Dinv, nn, ny, m, h->status, s, maxabs + 1));
+      RCI_CUDA_TRY(launch_gj<T>(D + nn, 2 * nn, Dinv, nn, ny, m, h->status, s, maxabs + 1,
+                                !h->simt));
     }
     // X_k = Dinv_k L_{2k+1};  Y_k = Dinv_k L_{2k+2}^T
     // D'_k = D_{2k} - L_{2k} Y_{k-1} (k >= 1) - L_{2k+1}^T X_k (k < m)
@@ -2040,7 +2049,8 @@ static cudaError_t factor_t(BcrHandle* h, const double2* dg, const double2* cx, 
         cudaError_t e;
         {
           ProfScope ps(h->prof, PF_GEMM, s, 8.0 * ny * (double)nn * (m + my), pb * 3.0 * (m + my), 1);
-          e = launch_tc_cgemm_tma_jobs(ny, ny, 2, xy, h->status, tc_wait_limit(), s);
+          e = h->simt ? cudaErrorNotSupported
+                      : launch_tc_cgemm_tma_jobs(ny, ny, 2, xy, h->status, tc_wait_limit(), s);
         }
         if (e == cudaSuccess) {
           ProfScope ps(h->prof, PF_GEMM, s, 8.0 * ny * (double)nn * (2 * (nk - 1) + m),
@@ -2054,17 +2064,17 @@ static cudaError_t factor_t(BcrHandle* h, const double2* dg, const double2* cx, 
     }
     if (!fused) {
       RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, false, one, Dinv, ny, nn, L + nn, ny, 2 * nn, zero,
-                           nullptr, 0, 0, X, ny, nn, m, s, h->prof, PF_GEMM, h->status));
+                           nullptr, 0, 0, X, ny, nn, m, s, h->prof, PF_GEMM, gemm_status(h)));
       RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, true, one, Dinv, ny, nn, L + 2 * nn, ny, 2 * nn, zero,
-                           nullptr, 0, 0, Y, ny, nn, my, s, h->prof, PF_GEMM, h->status));
+                           nullptr, 0, 0, Y, ny, nn, my, s, h->prof, PF_GEMM, gemm_status(h)));
       RCI_CUDA_TRY(cudaMemcpyAsync(Dn, D, nn * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s));
       RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, false, mone, L + 2 * nn, ny, 2 * nn, Y, ny, nn, one,
                            D + 2 * nn, ny, 2 * nn, Dn + nn, ny, nn, nk - 1, s, h->prof, PF_GEMM,
-                           h->status));
+                           gemm_status(h)));
       RCI_CUDA_TRY(gemm<T>(ny, ny, ny, true, false, mone, L + nn, ny, 2 * nn, X, ny, nn, one, Dn,
-                           ny, nn, Dn, ny, nn, m, s, h->prof, PF_GEMM, h->status));
+                           ny, nn, Dn, ny, nn, m, s, h->prof, PF_GEMM, gemm_status(h)));
       RCI_CUDA_TRY(gemm<T>(ny, ny, ny, false, false, mone, L + 2 * nn, ny, 2 * nn, X, ny, nn, zero,
-                           nullptr, 0, 0, Ln + nn, ny, nn, nk - 1, s, h->prof, PF_GEMM, h->status));
+                           nullptr, 0, 0, Ln + nn, ny, nn, nk - 1, s, h->prof, PF_GEMM, gemm_status(h)));
     }
     cur = 1 - cur;
   }
@@ -2072,7 +2082,7 @@ static cudaError_t factor_t(BcrHandle* h, const double2* dg, const double2* cx, 
   {
     ProfScope ps(h->prof, PF_INVERT, s, 8.0 * ny * (double)nn, 2.0 * nn * sizeof(cplx<T>), 1);
     RCI_CUDA_TRY(launch_gj<T>((cplx<T>*)h->Dw[cur], 0, store + h->final_off, 0, ny, 1, h->status, s,
-                              maxabs + 1));
+                              maxabs + 1, !h->simt));
   }
   return cudaSuccess;
 }
@@ -2260,7 +2270,7 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
   // ---- level 0 forward: t0[k] = T_{2k+1}^{-1} b[2k+1] with the stored inverses
   if (m0 > 0)
     RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, one, G0, ny, nn, b + row, nrhs, 2 * row, zero,
-                         nullptr, 0, 0, t0, nrhs, row, m0, s, nullptr, PF_SOLVE, h->status));
+                         nullptr, 0, 0, t0, nrhs, row, m0, s, nullptr, PF_SOLVE, gemm_status(h)));
   {
     int64_t nt = (int64_t)n1 * row;
     keep0_kernel<T><<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(b, t0, cx, B[1], nx, ny, n1, nrhs);
@@ -2276,11 +2286,11 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
     const cplx<T>* Y = X + (int64_t)m * nn;
     const cplx<T>* Bodd = B[l] + row;
     RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, one, Dinv, ny, nn, Bodd, nrhs, 2 * row, zero,
-                         nullptr, 0, 0, tl[l], nrhs, row, m, s, nullptr, PF_SOLVE, h->status));
+                         nullptr, 0, 0, tl[l], nrhs, row, m, s, nullptr, PF_SOLVE, gemm_status(h)));
     RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, true, false, one, X, ny, nn, Bodd, nrhs, 2 * row, zero,
-                         nullptr, 0, 0, P, nrhs, row, m, s, nullptr, PF_SOLVE, h->status));
+                         nullptr, 0, 0, P, nrhs, row, m, s, nullptr, PF_SOLVE, gemm_status(h)));
     RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, true, false, one, Y, ny, nn, Bodd, nrhs, 2 * row, zero,
-                         nullptr, 0, 0, Q, nrhs, row, my, s, nullptr, PF_SOLVE, h->status));
+                         nullptr, 0, 0, Q, nrhs, row, my, s, nullptr, PF_SOLVE, gemm_status(h)));
     int64_t nt = (int64_t)nk * row;
     keep_kernel<T><<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(B[l], P, Q, B[l + 1], m, nk, row);
     rci_note_launch();
@@ -2288,7 +2298,7 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
   }
   // ---- single remaining row
   RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, one, store + h->final_off, ny, 0, B[h->Lf], nrhs,
-                       0, zero, nullptr, 0, 0, xf, nrhs, 0, 1, s, nullptr, PF_SOLVE, h->status));
+                       0, zero, nullptr, 0, 0, xf, nrhs, 0, 1, s, nullptr, PF_SOLVE, gemm_status(h)));
   RCI_CUDA_TRY(cudaMemcpyAsync(B[h->Lf], xf, row * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s));
   // ---- dense levels backward (the solution of level l overwrites B[l])
   for (int l = h->Lf - 1; l >= 1; --l) {
@@ -2302,9 +2312,9 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
     rci_note_launch();
     RCI_CUDA_TRY(cudaGetLastError());
     RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, mone, X, ny, nn, B[l + 1], nrhs, row, one,
-                         tl[l], nrhs, row, B[l] + row, nrhs, 2 * row, m, s, nullptr, PF_SOLVE, h->status));
+                         tl[l], nrhs, row, B[l] + row, nrhs, 2 * row, m, s, nullptr, PF_SOLVE, gemm_status(h)));
     RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, mone, Y, ny, nn, B[l + 1] + row, nrhs, row,
-                         one, B[l] + row, nrhs, 2 * row, B[l] + row, nrhs, 2 * row, my, s, nullptr, PF_SOLVE, h->status));
+                         one, B[l] + row, nrhs, 2 * row, B[l] + row, nrhs, 2 * row, my, s, nullptr, PF_SOLVE, gemm_status(h)));
   }
   // ---- level 0 backward: x[2k+1] = T^{-1}(b[2k+1] - couplings x), stored inverses
   {
@@ -2316,7 +2326,7 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
     RCI_CUDA_TRY(cudaGetLastError());
     if (m0 > 0)
       RCI_CUDA_TRY(gemm<T>(ny, nrhs, ny, false, false, one, G0, ny, nn, t0, nrhs, row, zero,
-                           nullptr, 0, 0, x + row, nrhs, 2 * row, m0, s, nullptr, PF_SOLVE, h->status));
+                           nullptr, 0, 0, x + row, nrhs, 2 * row, m0, s, nullptr, PF_SOLVE, gemm_status(h)));
   }
   return cudaSuccess;
 }

@@ -42,6 +42,14 @@ cudaError_t bcr_solve(BcrHandle* h, const double2* cx, const void* b, void* x, i
 // blocks it inverted (the Schur complements of every level) over that of A's coefficients.
 cudaError_t bcr_read_status(BcrHandle* h, int32_t* st, cudaStream_t s, double* growth = nullptr);
 int bcr_precision(const BcrHandle* h);
+// Arithmetic of an FP32 handle from its next bcr_factor on: false (the default) runs the block
+// inversions and the products of the factorisation and of the several-right-hand-side solve
+// on the tensor cores (3xTF32 products accumulated in FP32, about 3.5 times the error of one
+// FP32 rounding per product); true runs them on the FP32 SIMT pipe (the Gauss-Jordan and
+// GEMM kernels of this file: one rounding per FMA, several times slower).  FP64 handles
+// ignore it.
+void bcr_set_simt(BcrHandle* h, bool simt);
+bool bcr_simt(const BcrHandle* h);
 // Optional profiler (owned by the caller) for the factor / solve kernel families.
 void bcr_set_profiler(BcrHandle* h, Profiler* p);
 

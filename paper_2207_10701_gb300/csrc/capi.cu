@@ -592,6 +592,67 @@ rci_status krylov_refine(rci_grid* g, const double2* b, double2* x, double2* r, 
 // correction) and b32 is unused.  An FP32 grid refines while each step reduces the
 // residual at least 0.7-fold, up to max_refine32 steps; a non-finite residual, stagnation
 // or running out of steps switches it to its FP64 fallback factorisation.
+// FP32 refinement on the grid's FP32 factorisation: x = M^-1 b, then corrections while the
+// FP64 stencil residual is above tol32; a single right-hand side whose plain refinement
+// stalls continues with the Krylov refinement within the same step budget.  *need64: the
+// factorisation could not resolve the system (non-finite residual, or refinement stalled
+// or out of steps); *it: refinement steps (the first solve not counted), *kry: Krylov steps.
+rci_status fp32_refine(rci_grid* g, const double2* b, double2* x, double2* r, void* a32,
+                       void* b32, int nrhs, int* it_out, int* kry_out, double* worst,
+                       bool* need64) {
+  const int64_t n = g->N * nrhs;
+  int it = 0, kry = 0;
+  *need64 = false;
+  CK(cudaMemsetAsync(x, 0, sizeof(double2) * n, g->s), "zero x");
+  CK(cudaMemcpyAsync(r, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, g->s), "copy b");
+  double prev = 1.0;
+  while (true) {
+    CK(launch_to_f32(r, (float2*)a32, n, g->s), "to fp32");
+    CK(bcr_solve(g->bcr, g->cx, a32, b32, nrhs, g->s), "fp32 solve");
+    CK(launch_add_f32(x, (const float2*)b32, n, g->s), "update");
+    ++it;
+    rci_status st = residual_ratio(g, b, x, r, nrhs, worst);
+    if (st == RCI_ENUMERIC) {
+      *need64 = true;
+      break;
+    }
+    if (st != RCI_OK) return st;
+    if (*worst <= g->tol32) break;
+    if (it >= g->max_refine32 || (it >= 3 && *worst > 0.7 * prev)) {
+      // plain refinement stalled: one right-hand side continues with the Krylov
+      // refinement within the remaining step budget
+      if (nrhs == 1 && it < g->max_refine32) {
+        int ks = 0;
+        st = krylov_refine(g, b, x, r, a32, b32, g->max_refine32 - it, &ks, worst);
+        it += ks;
+        kry = ks;
+        if (st == RCI_OK && *worst <= g->tol32) break;
+        if (st != RCI_OK && st != RCI_ENUMERIC) return st;
+      }
+      *need64 = true;
+      break;
+    }
+    prev = *worst;
+  }
+  *it_out = it - 1;  // the first FP32 solve is not a refinement step
+  *kry_out = kry;
+  return RCI_OK;
+}
+
+// Factor the current design again with the FP32 factorisation on the SIMT pipe, after its
+// tensor-core factorisation (3xTF32 products) could not resolve the system: one rounding per
+// FMA is enough for designs that the 3.5-fold larger product error tips over, at a fraction
+// of the cost of the FP64 factorisation.  *ok: the factorisation met no zero pivot.
+rci_status simt_refactor(rci_grid* g, bool* ok) {
+  *ok = false;
+  bcr_set_simt(g->bcr, true);
+  CK(bcr_factor(g->bcr, g->dg, g->cx, g->cy, g->s), "FP32 SIMT factor");
+  int32_t st = 0;
+  CK(bcr_read_status(g->bcr, &st, g->s, &g->growth), "FP32 SIMT factor status");
+  *ok = st == DEV_OK;
+  return RCI_OK;
+}
+
 rci_status refined_solve(rci_grid* g, const double2* b, double2* x, double2* r, void* a32,
                          void* b32, int nrhs, rci_info* info) {
   const int64_t n = g->N * nrhs;
@@ -605,38 +666,18 @@ rci_status refined_solve(rci_grid* g, const double2* b, double2* x, double2* r, 
   } else {
     bool need64 = g->use64;
     if (!need64) {
-      CK(cudaMemsetAsync(x, 0, sizeof(double2) * n, g->s), "zero x");
-      CK(cudaMemcpyAsync(r, b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, g->s), "copy b");
-      double prev = 1.0;
-      while (true) {
-        CK(launch_to_f32(r, (float2*)a32, n, g->s), "to fp32");
-        CK(bcr_solve(g->bcr, g->cx, a32, b32, nrhs, g->s), "fp32 solve");
-        CK(launch_add_f32(x, (const float2*)b32, n, g->s), "update");
-        ++it;
-        st = residual_ratio(g, b, x, r, nrhs, &worst);
-        if (st == RCI_ENUMERIC) {
-          need64 = true;
-          break;
-        }
+      st = fp32_refine(g, b, x, r, a32, b32, nrhs, &it, &kry, &worst, &need64);
+      if (st != RCI_OK) return st;
+      if (need64 && !bcr_simt(g->bcr)) {
+        // precision ladder: the FP32 SIMT factorisation before the FP64 one
+        bool ok = false;
+        st = simt_refactor(g, &ok);
         if (st != RCI_OK) return st;
-        if (worst <= g->tol32) break;
-        if (it >= g->max_refine32 || (it >= 3 && worst > 0.7 * prev)) {
-          // plain refinement stalled: one right-hand side continues with the Krylov
-          // refinement within the remaining step budget before the FP64 fallback
-          if (nrhs == 1 && it < g->max_refine32) {
-            int ks = 0;
-            st = krylov_refine(g, b, x, r, a32, b32, g->max_refine32 - it, &ks, &worst);
-            it += ks;
-            kry = ks;
-            if (st == RCI_OK && worst <= g->tol32) break;
-            if (st != RCI_OK && st != RCI_ENUMERIC) return st;
-          }
-          need64 = true;
-          break;
+        if (ok) {
+          st = fp32_refine(g, b, x, r, a32, b32, nrhs, &it, &kry, &worst, &need64);
+          if (st != RCI_OK) return st;
         }
-        prev = worst;
       }
-      it -= 1;  // the first FP32 solve is not a refinement step
     }
     if (need64) {
       st = fp64_fallback(g);
@@ -655,6 +696,7 @@ rci_status refined_solve(rci_grid* g, const double2* b, double2* x, double2* r, 
     info->fallback = fell_back ? 1 : 0;
     info->growth_est = fell_back ? g->growth64 : g->growth;
     info->krylov_steps = kry;
+    info->simt_refactor = bcr_simt(g->bcr) ? 1 : 0;
   }
   if (nrhs > 1) {  // the multi-RHS solve runs tensor-core GEMMs with bounded waits
     int32_t dst = 0;
@@ -693,7 +735,7 @@ rci_status run_angles(rci_grid* g, const rci_objective* o, const double* th_dev,
   int chunk = nq < MAXQ ? nq : MAXQ;
   st = ensure_multi(g, chunk);
   if (st != RCI_OK) return st;
-  int worst_it = 0;
+  int worst_it = 0, fb = 0, sr = 0;
   double worst_res = 0.0;
   rci_status agg = RCI_OK;
   for (int q0 = 0; q0 < nq; q0 += chunk) {
@@ -706,6 +748,8 @@ rci_status run_angles(rci_grid* g, const rci_objective* o, const double* th_dev,
     if (st == RCI_ENOCONV) agg = st;
     worst_it = ci.refine_iters > worst_it ? ci.refine_iters : worst_it;
     worst_res = ci.rel_residual > worst_res ? ci.rel_residual : worst_res;
+    fb |= ci.fallback;
+    sr |= ci.simt_refactor;
     if (o->kind == RCI_OBJ_POINT) {
       CK(launch_project_point(G, o->i_f, o->j_f, g->mx, c, c, f_dev + q0, g->s), "project");
     } else {
@@ -716,6 +760,8 @@ rci_status run_angles(rci_grid* g, const rci_objective* o, const double* th_dev,
   if (info) {
     info->refine_iters = worst_it;
     info->rel_residual = worst_res;
+    info->fallback = fb;
+    info->simt_refactor = sr;
     info->growth_est = g->use64 ? g->growth64 : g->growth;
   }
   return agg;
@@ -1009,6 +1055,7 @@ rci_status rci_set_design(rci_grid* g, const double* widths, int64_t n_cells, in
   g->has_design = true;
   g->factored = false;
   g->use64 = false;
+  bcr_set_simt(g->bcr, false);  // a new design starts on the tensor-core factorisation
   return RCI_OK;
 }
 
@@ -1030,8 +1077,17 @@ rci_status rci_factor(rci_grid* g) {
   if (st == DEV_TIMEOUT) return fail(g, RCI_ETIMEOUT, "a bounded tensor-core wait expired");
   if (st == DEV_SINGULAR) {
     if (g->d.prec == RCI_FP64) return fail(g, RCI_ESINGULAR, "zero pivot in a diagonal block");
-    rci_status fs = fp64_fallback(g);  // an FP32 pivot vanished: factor this design in FP64
-    if (fs != RCI_OK) return fs;
+    // an FP32 pivot vanished: factor this design again on the FP32 SIMT pipe and, if a pivot
+    // vanishes there too, in FP64
+    bool ok = false;
+    if (!bcr_simt(g->bcr)) {
+      rci_status ss = simt_refactor(g, &ok);
+      if (ss != RCI_OK) return ss;
+    }
+    if (!ok) {
+      rci_status fs = fp64_fallback(g);
+      if (fs != RCI_OK) return fs;
+    }
   }
   g->factored = true;
   return RCI_OK;
@@ -1173,6 +1229,7 @@ rci_status rci_avg_intensity_grad(rci_grid* g, const rci_objective* obj, const r
     info->fallback = i1.fallback | i2.fallback;
     info->growth_est = i2.growth_est > i1.growth_est ? i2.growth_est : i1.growth_est;
     info->krylov_steps = i1.krylov_steps + i2.krylov_steps;
+    info->simt_refactor = i1.simt_refactor | i2.simt_refactor;
     float ms = 0;
     cudaEventElapsedTime(&ms, g->ev[2], g->ev[3]);
     info->ms_solve = i1.ms_solve + ms;
@@ -1269,7 +1326,7 @@ rci_status rci_avg_intensity_multi(rci_grid* g, const rci_objective* objs, int64
   st = ensure_multi(g, chunk);
   if (st != RCI_OK) return st;
   const GridGeom& G = g->g;
-  int worst_it = 0, fb = 0;
+  int worst_it = 0, fb = 0, sr = 0;
   double worst_res = 0.0;
   rci_status agg = RCI_OK;
   for (int64_t o0 = 0; o0 < K; o0 += chunk) {
@@ -1287,6 +1344,7 @@ rci_status rci_avg_intensity_multi(rci_grid* g, const rci_objective* objs, int64
     worst_it = ci.refine_iters > worst_it ? ci.refine_iters : worst_it;
     worst_res = ci.rel_residual > worst_res ? ci.rel_residual : worst_res;
     fb |= ci.fallback;
+    sr |= ci.simt_refactor;
     for (int q = 0; q < c; ++q) {
       CK(launch_gather_source_col(G, g->mx, c, q, g->vsrc, g->s), "gather v");
       const double n = (double)G.n_src;
@@ -1309,6 +1367,7 @@ rci_status rci_avg_intensity_multi(rci_grid* g, const rci_objective* objs, int64
     info->refine_iters = worst_it;
     info->rel_residual = worst_res;
     info->fallback = fb;
+    info->simt_refactor = sr;
     info->growth_est = g->use64 ? g->growth64 : g->growth;
   }
   return agg;

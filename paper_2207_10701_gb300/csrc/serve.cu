@@ -230,6 +230,7 @@ void run_request(Request* r, rci_grid* g, bool hit, rci_result* res) {
   res->value = F;
   res->refine_iters = info.refine_iters;
   res->fp64_fallback = info.fallback;
+  res->simt_refactor = info.simt_refactor;
   res->rel_residual = info.rel_residual;
 }
 

@@ -46,7 +46,7 @@ class InfoC(C.Structure):
                 ("rel_residual", C.c_double), ("ms_factor", C.c_double),
                 ("ms_solve", C.c_double), ("ms_qform", C.c_double),
                 ("growth_est", C.c_double), ("krylov_steps", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("simt_refactor", C.c_int32)]
 
 
 class ServerDescC(C.Structure):
@@ -65,7 +65,8 @@ class ResultC(C.Structure):
                 ("refine_iters", C.c_int32), ("fp64_fallback", C.c_int32),
                 ("rel_residual", C.c_double), ("t_submit_us", C.c_double),
                 ("t_start_us", C.c_double), ("t_end_us", C.c_double),
-                ("footprint", C.c_uint64)]
+                ("footprint", C.c_uint64), ("simt_refactor", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class ServerStatsC(C.Structure):
@@ -101,11 +102,12 @@ class Info:
     fallback: bool = False
     growth_est: float = 0.0
     krylov_steps: int = 0
+    simt_refactor: bool = False
 
     @staticmethod
     def of(c: InfoC) -> "Info":
         return Info(c.refine_iters, c.rel_residual, c.ms_factor, c.ms_solve, c.ms_qform,
-                    bool(c.fallback), c.growth_est, c.krylov_steps)
+                    bool(c.fallback), c.growth_est, c.krylov_steps, bool(c.simt_refactor))
 
 
 class RciError(RuntimeError):
@@ -583,6 +585,7 @@ class Server:
         grad = self._grads.pop(ticket, None)
         return {"status": r.status, "value": r.value, "cache_hit": bool(r.cache_hit),
                 "refine_iters": r.refine_iters, "fp64_fallback": r.fp64_fallback,
+                "simt_refactor": r.simt_refactor,
                 "rel_residual": r.rel_residual,
                 "t_submit_us": r.t_submit_us, "t_start_us": r.t_start_us,
                 "t_end_us": r.t_end_us, "footprint": r.footprint, "grad": grad}
