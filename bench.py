@@ -596,7 +596,9 @@ def run_ours(args):
                 "workload": wg.name, "iterations": len(res.steps), "accepted": len(res.history) - 1,
                 "F_start": res.history[0], "F_end": res.history[-1],
                 "gain": round(res.history[-1] / res.history[0], 4),
-                "seconds": round(time.perf_counter() - t0, 2)}
+                "seconds": round(time.perf_counter() - t0, 2),
+                "evaluations": res.evaluations, "refine_iters_max": res.refine_iters_max,
+                "simt_refactors": res.simt_refactors, "fp64_fallbacks": res.fp64_fallbacks}
         # the precision form at 1000 wavelengths (2500 cells, nx 20040, ny 224, 4.5M unknowns,
         # virtual focus 50 wavelengths up, cone of +-20 degrees): cold FP32 + refinement
         # evaluations against the FP64 form of the same design, one grid at a time

@@ -56,6 +56,16 @@ class DesignResult:
     widths: np.ndarray
     history: list = field(default_factory=list)   # F after each accepted step
     steps: list = field(default_factory=list)     # step length used at each iteration
+    evaluations: int = 0        # evaluations with gradient
+    simt_refactors: int = 0     # of which finished on the FP32 SIMT refactorisation
+    fp64_fallbacks: int = 0     # of which finished on the FP64 factorisation
+    refine_iters_max: int = 0
+
+    def note(self, info) -> None:
+        self.evaluations += 1
+        self.simt_refactors += int(info.simt_refactor and not info.fallback)
+        self.fp64_fallbacks += int(info.fallback)
+        self.refine_iters_max = max(self.refine_iters_max, info.refine_iters)
 
 
 def optimize(grid: Grid, obj, light, widths0, iters: int = 100, step: float = 0.01,
@@ -69,8 +79,9 @@ def optimize(grid: Grid, obj, light, widths0, iters: int = 100, step: float = 0.
     w = np.clip(np.asarray(widths0, dtype=np.float64), lo, hi)
     grid.set_design(w)
     grid.factor()
-    F, g, _ = grid.avg_intensity_grad(obj, light)
+    F, g, info = grid.avg_intensity_grad(obj, light)
     res = DesignResult(widths=w.copy(), history=[F])
+    res.note(info)
     t = step
     for _ in range(iters):
         gmax = float(np.max(np.abs(g)))
@@ -79,7 +90,8 @@ def optimize(grid: Grid, obj, light, widths0, iters: int = 100, step: float = 0.
         trial = np.clip(w + t * g / gmax, lo, hi)
         grid.set_design(trial)
         grid.factor()
-        F1, g1, _ = grid.avg_intensity_grad(obj, light)
+        F1, g1, info = grid.avg_intensity_grad(obj, light)
+        res.note(info)
         res.steps.append(t)
         if F1 >= F:
             w, F, g = trial, F1, g1

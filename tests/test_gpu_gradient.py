@@ -219,3 +219,5 @@ def test_design_loop_c4_100_iterations():
     assert len(res.steps) == 100
     assert np.all(np.diff(h) >= 0) and h[-1] > h[0], (h[0], h[-1], len(h))
     assert np.all(res.widths >= 0.08) and np.all(res.widths <= 0.36)
+    # every evaluation of the ascent finishes in FP32 (plain or Krylov refinement)
+    assert res.evaluations == 101 and res.fp64_fallbacks == 0, res
