@@ -176,7 +176,8 @@ rci_status rci_factor(rci_grid* g);
 
 /* Solve A x = b for nrhs right-hand sides stored [i][j][q] (q fastest):
  * b, x: DEVICE complex128[nx*ny*nrhs].  x may alias b.  FP32_REFINE grids refine
- * every right-hand side with the FP64 stencil residual to rel. residual 1e-12;
+ * every right-hand side with the FP64 stencil residual to the grid's tolerance (rel.
+ * residual 1e-10 by default, rci_set_refinement);
  * FP64 grids take up to two refinement steps.  info (HOST, may be NULL). */
 rci_status rci_solve(rci_grid* g, const double* b, double* x, int64_t nrhs, rci_info* info);
 
