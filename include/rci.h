@@ -170,8 +170,12 @@ rci_status rci_grid_query(const rci_grid* g, int64_t* nx, int64_t* ny, int64_t* 
 rci_status rci_set_design(rci_grid* g, const double* widths, int64_t n_cells, int widths_on_device);
 
 /* Factor A by block cyclic reduction along x (the direct solver behind every
- * solve; Sec. 4.1 asks for one solve per evaluation).  Precision per grid.
- * Errors: ESTATE (no design), ESINGULAR (zero pivot in a diagonal block). */
+ * solve; Sec. 4.1 asks for one solve per evaluation).  Precision per grid.  An
+ * FP32_REFINE grid whose factorisation meets a zero pivot factors the design again on
+ * the FP32 SIMT pipe and, if a pivot vanishes there too, in FP64 (rci_set_refinement).
+ * Errors: ESTATE (no design), ESINGULAR (zero pivot in a diagonal block of the FP64
+ * factorisation), EINVAL (a device width out of range), ETIMEOUT (an expired bounded
+ * wait of a tensor-core kernel). */
 rci_status rci_factor(rci_grid* g);
 
 /* Solve A x = b for nrhs right-hand sides stored [i][j][q] (q fastest):
