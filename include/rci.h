@@ -80,7 +80,9 @@ typedef enum {
 /* Problem geometry (lengths in wavelengths, counts in grid cells). */
 typedef struct {
   int32_t n_cells;      /* unit cells (one pillar each) */
-  int32_t ny;           /* rows, PML included */
+  int32_t ny;           /* rows, PML included: 4 .. 256 (the single-right-hand-side solve
+                           holds a row of the stored blocks in registers); even for FP32_REFINE
+                           (rows are read as pairs of complex64) */
   int32_t ppl;          /* grid points per wavelength, h = 1/ppl */
   int32_t cell_px;      /* unit-cell period in cells */
   int32_t npml;         /* PML thickness in cells on all four sides */

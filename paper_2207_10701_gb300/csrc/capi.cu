@@ -133,8 +133,14 @@ bool desc_ok(const rci_grid_desc* d, std::string& why) {
     why = "ny leaves no air rows above the pillars";
     return false;
   }
-  if (d->ny > 1024) {
-    why = "ny > 1024 is not supported";
+  if (d->ny > 256) {
+    // the single-right-hand-side solve holds the row vectors of the stored blocks in
+    // registers (ny / 32 16-byte vectors per lane and row in FP64, the FP32 grid's fallback)
+    why = "ny > 256 is not supported";
+    return false;
+  }
+  if (d->prec == RCI_FP32_REFINE && (d->ny & 1)) {
+    why = "FP32_REFINE grids need an even ny (rows are read as pairs of complex64)";
     return false;
   }
   if (!(d->eps_pillar > 0 && d->eps_sub > 0 && d->eps_air > 0) || !(d->pml_R0 > 0 && d->pml_R0 < 1) ||

@@ -54,3 +54,20 @@ def test_invalid_descriptor_is_rejected_without_a_device(libpath):
     h = C.c_void_p()
     assert R.lib().rci_create_grid(C.byref(d), None, C.byref(h)) == 1   # RCI_EINVAL
     assert R.lib().rci_qform_toeplitz(None, None, 0, None, None) == 1
+
+
+def test_descriptor_limits_of_the_solver_are_checked_at_creation(libpath):
+    # the footprint query validates a descriptor exactly as grid creation does, on the host
+    import ctypes as C
+    import paper_2207_10701_gb300.rci as R
+    import workloads as W
+
+    def footprint(ny, prec):
+        d = R._desc(W.GridDesc(n_cells=2, ny=ny, prec=prec))
+        b = C.c_size_t()
+        return R.lib().rci_grid_footprint(C.byref(d), 0, C.byref(b))
+
+    assert footprint(256, R.FP64) == 0 and footprint(256, R.FP32_REFINE) == 0
+    assert footprint(258, R.FP64) == 1 and footprint(258, R.FP32_REFINE) == 1   # RCI_EINVAL
+    assert footprint(161, R.FP64) == 0
+    assert footprint(161, R.FP32_REFINE) == 1      # FP32 rows are read as complex64 pairs
