@@ -1745,6 +1745,67 @@ mv_chunk_kernel(const cplx<T>* __restrict__ M, const cplx<T>* __restrict__ V, in
   rows_mv<T, SMAX>(M + k * (int64_t)ny * ny, vs, ny, blockIdx.y * RC, y + k * ny, nullptr);
 }
 
+// Row r of a level's right-hand side formed from the level before it (Bp, its P, Q and
+// mp eliminated rows): b[r] = Bp[2r] - Qp[r-1] - Pp[r], the Q term for r >= 1 and the P term
+// for r < mp, in keep_kernel's order (so the values are the ones keep_kernel would store).
+template <typename T>
+__device__ __forceinline__ cplx<T> kept_row(const cplx<T>* __restrict__ Bp,
+                                            const cplx<T>* __restrict__ Pp,
+                                            const cplx<T>* __restrict__ Qp, int mp, int64_t r,
+                                            int c, int ny) {
+  cplx<T> v = Bp[2 * r * ny + c];
+  if (r >= 1) v = v - Qp[(r - 1) * ny + c];
+  if (r < mp) v = v - Pp[r * ny + c];
+  return v;
+}
+
+// Dense level l >= 2, forward, with the kept-row update of level l - 1 fused in: block
+// (k, chunk) forms the odd row 2k + 1 of this level's right-hand side whole in shared memory
+// and then t_k, P_k, Q_k on its chunk as fwd_chunk_kernel does; it also writes the even row
+// 2k on its chunk to Bn, from which the next level forms its rows.  Grid (ceil(n / 2),
+// ceil(ny / RC)): for odd n the last block row k = n / 2 has its even row only.
+template <typename T, int SMAX>
+__global__ void __launch_bounds__(CH_THREADS)
+fwd_keep_chunk_kernel(const cplx<T>* __restrict__ Dinv, const cplx<T>* __restrict__ X,
+                      const cplx<T>* __restrict__ Y, const cplx<T>* __restrict__ Bp,
+                      const cplx<T>* __restrict__ Pp, const cplx<T>* __restrict__ Qp, int mp,
+                      cplx<T>* __restrict__ Bn, cplx<T>* __restrict__ t, cplx<T>* __restrict__ P,
+                      cplx<T>* __restrict__ Q, int n, int ny) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cplx<T>* bs = reinterpret_cast<cplx<T>*>(sm_raw);
+  cplx<T>* red = bs + ny;
+  const int64_t k = blockIdx.x;
+  const int c0 = blockIdx.y * RC;
+  const int64_t nn = (int64_t)ny * ny;
+  for (int c = c0 + threadIdx.x; c < c0 + RC && c < ny; c += CH_THREADS)
+    Bn[2 * k * ny + c] = kept_row<T>(Bp, Pp, Qp, mp, 2 * k, c, ny);
+  if (2 * k + 1 >= n) return;  // (uniform over the block)
+  constexpr bool early = sizeof(T) == 4 && SMAX <= 3;
+  Rows1<T, early ? SMAX : 1> R;
+  if constexpr (early) rows_load1<T, SMAX>(R, Dinv + k * nn, ny, c0);
+  for (int c = threadIdx.x; c < ny; c += CH_THREADS)
+    bs[c] = kept_row<T>(Bp, Pp, Qp, mp, 2 * k + 1, c, ny);
+  __syncthreads();
+  if constexpr (early) rows_dot1<T, SMAX>(R, bs, ny, c0, t + k * ny);
+  else rows_mv<T, SMAX>(Dinv + k * nn, bs, ny, c0, t + k * ny, nullptr);
+  cols_mvT2<T>(X + k * nn, 2 * k + 2 < n ? Y + k * nn : nullptr, bs, ny, c0, red, P + k * ny,
+               Q + k * ny);
+}
+
+// The single last row with the kept-row update of the level before it fused in:
+// y = M b[0], b[0] = Bp[0] - Pp[0] (mp > 0).  Grid (1, ceil(ny / RC)).
+template <typename T, int SMAX>
+__global__ void __launch_bounds__(CH_THREADS)
+mv_keep_chunk_kernel(const cplx<T>* __restrict__ M, const cplx<T>* __restrict__ Bp,
+                     const cplx<T>* __restrict__ Pp, const cplx<T>* __restrict__ Qp, int mp,
+                     cplx<T>* __restrict__ y, int ny) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  cplx<T>* vs = reinterpret_cast<cplx<T>*>(sm_raw);
+  for (int c = threadIdx.x; c < ny; c += CH_THREADS) vs[c] = kept_row<T>(Bp, Pp, Qp, mp, 0, c, ny);
+  __syncthreads();
+  rows_mv<T, SMAX>(M, vs, ny, blockIdx.y * RC, y, nullptr);
+}
+
 // ----- single right-hand side, level 0 by the pivoted tridiagonal factors (5 ny values per
 // eliminated row instead of the dense ny x ny inverse): one warp per eliminated row k stages
 // the row's factors and right-hand side in shared memory, lane 0 runs the forward and
@@ -2100,8 +2161,8 @@ static int64_t ws_elems(const BcrHandle* h, int nrhs) {
   int64_t tot = h->m[0] * row;
   for (int l = 1; l <= h->Lf; ++l) tot += h->n[l] * row;
   for (int l = 1; l < h->Lf; ++l) tot += h->m[l] * row;
-  int64_t m1 = h->Lf > 1 ? h->m[1] : 0;
-  tot += 2 * m1 * row + row;
+  int64_t m1 = h->Lf > 1 ? h->m[1] : 0, m2 = h->Lf > 2 ? h->m[2] : 0;
+  tot += 2 * m1 * row + 2 * m2 * row + row;  // P, Q of the odd levels, of the even levels, xf
   return tot;
 }
 
@@ -2136,11 +2197,17 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
     tl[l] = p;
     p += h->m[l] * row;
   }
-  int64_t m1 = h->Lf > 1 ? h->m[1] : 0;
+  int64_t m1 = h->Lf > 1 ? h->m[1] : 0, m2 = h->Lf > 2 ? h->m[2] : 0;
   cplx<T>* P = p;
   p += m1 * row;
   cplx<T>* Q = p;
   p += m1 * row;
+  // a second pair for the even levels: one right-hand side forms a level's rows from the P
+  // and Q of the level before while it writes its own
+  cplx<T>* P2 = p;
+  p += m2 * row;
+  cplx<T>* Q2 = p;
+  p += m2 * row;
   cplx<T>* xf = p;
 
   auto store = (const cplx<T>*)h->store;
@@ -2161,7 +2228,7 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
   // single remaining row); several right-hand sides run the level products as GEMMs
   {
     const int dense = h->Lf - 1, l0 = m0 > 0 ? 1 : 0;
-    ps.nl = nrhs == 1 ? l0 + 1 + 2 * dense + 1 + dense + 1
+    ps.nl = nrhs == 1 ? l0 + 1 + dense + 1 + dense + 1
                       : l0 + 1 + 4 * dense + 1 + 3 * dense + 1 + l0;
   }
 
@@ -2212,22 +2279,34 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
       rci_note_launch();
       RCI_CUDA_TRY(cudaGetLastError());
     }
-    // ---- dense levels forward
+    // ---- dense levels forward: level 1 from the kept rows of level 0; every later level forms
+    // its rows from the level before (the kept-row update fused into its forward kernel), the
+    // P and Q of odd levels in (P, Q), of even levels in (P2, Q2)
+    auto Pl = [&](int l) { return (l & 1) ? P : P2; };
+    auto Ql = [&](int l) { return (l & 1) ? Q : Q2; };
     for (int l = 1; l < h->Lf; ++l) {
-      const int n = (int)h->n[l], m = (int)h->m[l], nk = (int)h->n[l + 1];
+      const int n = (int)h->n[l], m = (int)h->m[l];
       const cplx<T>* Dinv = store + h->off[l];
       const cplx<T>* X = Dinv + (int64_t)m * nn;
       const cplx<T>* Y = X + (int64_t)m * nn;
-      RCI_SMAX_DISPATCH(fwd_chunk_kernel, dim3(m, nch), ny * sizeof(cplx<T>) + red_smem, Dinv, X,
-                        Y, B[l], tl[l], P, Q, n, ny);
-      int64_t nt = (int64_t)nk * row;
-      keep_kernel<T><<<(unsigned)ceil_div(nt, 256), 256, 0, s>>>(B[l], P, Q, B[l + 1], m, nk, row);
-      rci_note_launch();
-      RCI_CUDA_TRY(cudaGetLastError());
+      if (l == 1) {
+        RCI_SMAX_DISPATCH(fwd_chunk_kernel, dim3(m, nch), ny * sizeof(cplx<T>) + red_smem, Dinv,
+                          X, Y, B[1], tl[1], Pl(1), Ql(1), n, ny);
+      } else {
+        RCI_SMAX_DISPATCH(fwd_keep_chunk_kernel, dim3((unsigned)h->n[l + 1], nch),
+                          ny * sizeof(cplx<T>) + red_smem, Dinv, X, Y, B[l - 1], Pl(l - 1),
+                          Ql(l - 1), (int)h->m[l - 1], B[l], tl[l], Pl(l), Ql(l), n, ny);
+      }
     }
-    // ---- single remaining row
-    RCI_SMAX_DISPATCH(mv_chunk_kernel, dim3(1, nch), ny * sizeof(cplx<T>), store + h->final_off,
-                      B[h->Lf], (int64_t)0, (int64_t)0, xf, ny);
+    // ---- single remaining row (from the level before it when there is one)
+    if (h->Lf >= 2) {
+      const int lp = h->Lf - 1;
+      RCI_SMAX_DISPATCH(mv_keep_chunk_kernel, dim3(1, nch), ny * sizeof(cplx<T>),
+                        store + h->final_off, B[lp], Pl(lp), Ql(lp), (int)h->m[lp], xf, ny);
+    } else {
+      RCI_SMAX_DISPATCH(mv_chunk_kernel, dim3(1, nch), ny * sizeof(cplx<T>), store + h->final_off,
+                        B[h->Lf], (int64_t)0, (int64_t)0, xf, ny);
+    }
     RCI_CUDA_TRY(cudaMemcpyAsync(B[h->Lf], xf, row * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s));
     // ---- dense levels backward (the solution of level l overwrites B[l])
     for (int l = h->Lf - 1; l >= 1; --l) {

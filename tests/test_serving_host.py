@@ -46,7 +46,8 @@ def _expected_footprint(d: W.GridDesc, fp64: bool, grad: bool) -> int:
     sizes += [m0b * esz] * 4 + [m0b, m0b * ny * esz]
     sizes += [n1 * nn * esz] * 4 + [(off + nn) * esz, 4]
     ws = m0 * ny + sum(n[l] * ny for l in range(1, Lf + 1)) + \
-        sum(m[l] * ny for l in range(1, Lf)) + 2 * (m[1] if Lf > 1 else 0) * ny + ny
+        sum(m[l] * ny for l in range(1, Lf)) + 2 * (m[1] if Lf > 1 else 0) * ny + \
+        2 * (m[2] if Lf > 2 else 0) * ny + ny
     sizes.append(ws * esz)
     if grad:
         sizes += [16 * N, 16 * ns, 16 * ns * math.ceil(ns / 1024), 8 * d.n_cells]
