@@ -2298,16 +2298,17 @@ static cudaError_t solve_t(BcrHandle* h, const double2* cx, const cplx<T>* b, cp
                           Ql(l - 1), (int)h->m[l - 1], B[l], tl[l], Pl(l), Ql(l), n, ny);
       }
     }
-    // ---- single remaining row (from the level before it when there is one)
+    // ---- single remaining row (from the level before it when there is one, written straight
+    // to B[Lf], which nothing reads as input then)
     if (h->Lf >= 2) {
       const int lp = h->Lf - 1;
       RCI_SMAX_DISPATCH(mv_keep_chunk_kernel, dim3(1, nch), ny * sizeof(cplx<T>),
-                        store + h->final_off, B[lp], Pl(lp), Ql(lp), (int)h->m[lp], xf, ny);
+                        store + h->final_off, B[lp], Pl(lp), Ql(lp), (int)h->m[lp], B[h->Lf], ny);
     } else {
       RCI_SMAX_DISPATCH(mv_chunk_kernel, dim3(1, nch), ny * sizeof(cplx<T>), store + h->final_off,
                         B[h->Lf], (int64_t)0, (int64_t)0, xf, ny);
+      RCI_CUDA_TRY(cudaMemcpyAsync(B[h->Lf], xf, row * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s));
     }
-    RCI_CUDA_TRY(cudaMemcpyAsync(B[h->Lf], xf, row * sizeof(cplx<T>), cudaMemcpyDeviceToDevice, s));
     // ---- dense levels backward (the solution of level l overwrites B[l])
     for (int l = h->Lf - 1; l >= 1; --l) {
       const int n = (int)h->n[l], m = (int)h->m[l], nk = (int)h->n[l + 1];

@@ -101,7 +101,9 @@ def test_lookahead_lets_a_small_request_overtake():
         outs = [srv.wait(t, timeout=600) for t in t_big]
         st = srv.stats()
     assert st["bypasses"] >= 1
-    assert out_small["t_end_us"] < outs[2]["t_start_us"]   # finished before the 3rd big one began
+    # the arena holds one big request at a time: the small one, submitted last, is admitted
+    # while the second big one waits for the first (admission order, not execution speed)
+    assert out_small["t_start_us"] < outs[1]["t_start_us"]
     assert out_small["value"] == _alone(small, P.FP32_REFINE)[0]
     for r, out in zip(big, outs):
         assert out["status"] == 0 and out["value"] == _alone(r, P.FP32_REFINE)[0]
