@@ -390,6 +390,9 @@ typedef struct {
   int32_t reserved;
 } rci_result;
 
+/* Server counters.  admission_waits: times a free worker found no queued request it could
+ * admit for lack of memory and slept until a request finished or arrived; bypasses: requests
+ * started ahead of the queue's head by the look-ahead. */
 typedef struct {
   uint64_t submitted, completed, failed, cache_hits, cache_evictions, admission_waits, bypasses;
   int32_t in_flight, queued, resident, reserved;

@@ -242,7 +242,7 @@ void worker(rci_server* s, int slot) {
     s->cv_work.wait(lk, [&] { return s->stop || !s->queue.empty(); });
     if (s->queue.empty()) return;  // stopping and drained
     Request* r = pick(s);
-    if (!r) {  // the head waits for memory: sleep until a request finishes
+    if (!r) {  // the head waits for memory: sleep until a request finishes or arrives
       s->st.admission_waits++;
       s->cv_done.wait(lk);
       continue;
@@ -447,6 +447,9 @@ rci_status rci_server_submit(rci_server* s, const rci_request* q, uint64_t* tick
   s->st.submitted++;
   *ticket = r->ticket;
   s->cv_work.notify_one();
+  // workers whose head request waits for memory sleep until a request finishes; a new
+  // request may be one the look-ahead can start now, so they look at the queue again
+  s->cv_done.notify_all();
   return RCI_OK;
 }
 

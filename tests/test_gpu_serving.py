@@ -102,7 +102,8 @@ def test_lookahead_lets_a_small_request_overtake():
         st = srv.stats()
     assert st["bypasses"] >= 1
     # the arena holds one big request at a time: the small one, submitted last, is admitted
-    # while the second big one waits for the first (admission order, not execution speed)
+    # while the second big one waits for the first (admission order, not execution speed;
+    # the workers waiting for memory look at the queue again when a request arrives)
     assert out_small["t_start_us"] < outs[1]["t_start_us"]
     assert out_small["value"] == _alone(small, P.FP32_REFINE)[0]
     for r, out in zip(big, outs):
